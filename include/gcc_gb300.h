@@ -1,0 +1,276 @@
+/*
+ * gcc_gb300.h -- C ABI of the GPU concurrency-control engine (sm_103a).
+ *
+ * The engine executes a batch of OLTP transactions concurrently on one GPU
+ * under one of four concurrency-control schemes and returns, per transaction,
+ * its commit status, its position in a commit order and the values it read.
+ * It follows the paper's statement of the problem: transactions are run in
+ * batches, one worker per transaction (Sec. III-B); read and write sets are
+ * known before execution (Sec. IV-A, "Constraints"); an aborted transaction
+ * restarts until it commits (Sec. IV-A, "Experimental Procedure"); every scheme
+ * is serializable (Sec. III-E).  The committed transactions, executed serially
+ * in the reported commit order from the same initial database, produce exactly
+ * the reported reads and the final database.
+ *
+ * Conventions for every call:
+ *  - Return value: GCC_OK or an error code; gcc_last_error() then gives a
+ *    message (thread-local, valid until the next failing call on the thread).
+ *  - Pointers are plain host or device pointers as stated per argument; no
+ *    call takes ownership of caller memory.  Objects returned through `out`
+ *    parameters are owned by the library until their destroy/free call.
+ *  - Calls on one database must be ordered: issue them from one host thread
+ *    and, for the asynchronous ones, on one stream (a NULL stream means the
+ *    database's own stream).
+ *  - Multi-byte fields are little-endian; structs below have no implicit
+ *    padding.
+ */
+#ifndef GCC_GB300_H
+#define GCC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gcc_status {
+    GCC_OK = 0,
+    GCC_ERR_INVALID = 1,   /* bad argument or malformed batch                   */
+    GCC_ERR_CUDA = 2,      /* a CUDA runtime call failed                        */
+    GCC_ERR_TIMEOUT = 3,   /* host wait ran out, or a device budget was spent   */
+    GCC_ERR_NOMEM = 4,     /* device or host allocation failed                  */
+    GCC_ERR_DEVICE = 5,    /* the kernel reported an error flag (see stats)     */
+    GCC_ERR_CAPACITY = 6   /* batch larger than the database was created for    */
+} gcc_status;
+
+/* Concurrency-control schemes (Sec. II, Table I; Sec. III-E). */
+typedef enum gcc_scheme {
+    GCC_NO_WAIT_2PL = 0,   /* two-phase locking, abort when a lock is taken     */
+    GCC_TO = 1,            /* basic timestamp ordering with a commit (dirty) bit */
+    GCC_OCC = 2,           /* read-validate-write OCC with commit timestamps    */
+    GCC_DET = 3            /* deterministic conflict-ordered batch (GPUTx-like) */
+} gcc_scheme;
+
+typedef enum gcc_schema {
+    GCC_SCHEMA_KV = 0,           /* one table of n_records x n_fields slots      */
+    GCC_SCHEMA_ORDER_ENTRY = 1   /* TPC-C-shaped warehouse/district/customer/... */
+} gcc_schema;
+
+/* Op kinds.  Key-value: READ returns the slot; ADD returns the old slot and
+ * adds the operand (8-byte slots: modulo 2^64; 16-byte slots: lo modulo 2^64
+ * and bytes 8-9 as a u16 modulo 2^16, bytes 10-15 unchanged).
+ * Order-entry kinds implement the NewOrder and Payment procedures, one op per
+ * record access, in this fixed layout (row numbering as in the table ids
+ * below; reads are (lo, hi) pairs):
+ *   NewOrder: W_READ(w) -> (w_tax, 0); D_NEWORDER(district) -> (d_next_o_id,
+ *     d_tax), next_o_id += 1; C_READ(customer) -> (c_discount, c_balance);
+ *     then per line: I_READ(item) -> (i_price, 0), S_NEWORDER(stock row,
+ *     operand qty, remote) -> (s_quantity, s_order_cnt) with s_quantity -= qty
+ *     (+91 when the old quantity was below qty + 10), s_ytd += qty,
+ *     s_order_cnt += 1, s_remote_cnt += remote.  At commit the order
+ *     (o_id = the d_next_o_id read), its new-order flag and its lines
+ *     (amount = qty * i_price) are inserted.
+ *   Payment: W_PAY(w, h) -> (w_ytd, 0); D_PAY(district, h) -> (d_ytd, 0);
+ *     C_PAY(customer, h) -> (c_balance, c_payment_cnt), c_balance -= h,
+ *     c_ytd_payment += h, c_payment_cnt += 1. */
+enum gcc_op_kind {
+    GCC_OP_READ = 0,
+    GCC_OP_ADD = 1,
+    GCC_OE_W_READ = 16,
+    GCC_OE_W_PAY = 17,
+    GCC_OE_D_NEWORDER = 18,
+    GCC_OE_D_PAY = 19,
+    GCC_OE_C_READ = 20,
+    GCC_OE_C_PAY = 21,
+    GCC_OE_I_READ = 22,
+    GCC_OE_S_NEWORDER = 23
+};
+
+enum gcc_txn_type { GCC_TXN_KV = 0, GCC_TXN_NEW_ORDER = 1, GCC_TXN_PAYMENT = 2 };
+
+/* Per-transaction outcome. */
+enum gcc_txn_status {
+    GCC_TXN_PENDING = 0,     /* not executed (the batch was cut short)           */
+    GCC_TXN_COMMITTED = 1,
+    GCC_TXN_TIMEOUT = 2,     /* attempt budget, wait budget or deadline spent     */
+    GCC_TXN_INVALID = 3      /* bad key/field/kind, duplicate key, too many ops  */
+};
+
+/* A transaction: ops[first_op .. first_op + n_ops).  Transactions are given in
+ * transaction-id order (index = id); their op ranges must not overlap and must
+ * increase with the id.  GCC_DET orders conflicting accesses by op position,
+ * so there the ranges must tile ops[0 .. n_ops) exactly, in id order; an op
+ * outside every range makes later accesses to its record wait until
+ * wait_budget_ns runs out (GCC_TXN_TIMEOUT). */
+typedef struct gcc_txn {
+    uint32_t first_op;
+    uint16_t n_ops;
+    uint16_t type;           /* gcc_txn_type */
+} gcc_txn;
+
+/* An op descriptor.  key: record number (key-value) or row (order-entry);
+ * field: key-value field index; kind: gcc_op_kind.  Keys within one
+ * transaction must be distinct (record-granularity conflicts). */
+typedef struct gcc_op {
+    uint32_t key;
+    uint8_t field;
+    uint8_t kind;
+    uint16_t aux;            /* reserved, 0 */
+} gcc_op;
+
+/* An op operand or a value read: two 64-bit lanes. */
+typedef struct gcc_operand {
+    uint64_t lo;
+    uint64_t hi;
+} gcc_operand;
+
+typedef struct gcc_txn_result {
+    uint32_t status;         /* gcc_txn_status */
+    uint32_t attempts;       /* executions started, including the committing one */
+    uint64_t commit_order;   /* committed: 0..n_committed-1, a serial order;
+                                otherwise UINT64_MAX */
+} gcc_txn_result;
+
+typedef struct gcc_db_desc {
+    uint32_t schema;           /* gcc_schema */
+    uint32_t field_bytes;      /* key-value: 8 or 16 */
+    uint64_t n_records;        /* key-value: records (<= 2^31) */
+    uint32_t n_fields;         /* key-value: fields per record (1..255) */
+    uint32_t n_warehouses;     /* order-entry: W (1..1024) */
+    uint32_t order_cap;        /* order-entry: order slots per district (>= 3000) */
+    uint32_t max_ops_per_txn;  /* upper bound on gcc_txn.n_ops (1..64) */
+    uint64_t max_batch_txns;   /* upper bound on transactions per batch */
+    uint64_t max_batch_ops;    /* upper bound on ops per batch (< 2^32) */
+    int32_t device;            /* CUDA device ordinal */
+    uint32_t reserved;         /* 0 */
+} gcc_db_desc;
+
+/* Launch and retry policy.  Zero fields take the defaults in brackets. */
+typedef struct gcc_exec_params {
+    uint32_t lanes_per_txn;    /* lanes of a warp that cooperate on one
+                                  transaction: 1,2,4,8,16,32 [16] */
+    uint32_t warps_per_block;  /* 1..32 [8] */
+    uint32_t blocks_per_sm;    /* resident blocks per SM [occupancy limit] */
+    uint32_t collapse;         /* 1 = collapse same-key lock attempts inside a
+                                  warp before they reach global atomics [1];
+                                  2 = off */
+    uint32_t backoff_base_ns;  /* first retry delay, doubled per abort [0 = none] */
+    uint32_t backoff_cap_ns;   /* largest retry delay [100000] */
+    uint32_t max_attempts;     /* per transaction, then GCC_TXN_TIMEOUT [2^24] */
+    uint32_t read_retries;     /* re-reads of a record seen mid-update before
+                                  the attempt aborts [8] */
+    uint64_t wait_budget_ns;   /* deterministic scheme: bound on one wait [2 s] */
+    uint64_t deadline_ns;      /* whole-kernel budget, then remaining work ends
+                                  as GCC_TXN_TIMEOUT [60 s] */
+    uint64_t seed;             /* retry jitter and abort injection */
+    uint32_t inject_abort_ppm; /* test hook: abort an attempt at its commit point
+                                  with this probability per million [0] */
+    uint32_t reserved;         /* 0 */
+} gcc_exec_params;
+
+typedef struct gcc_batch_stats {
+    uint64_t n_txns;
+    uint64_t committed;
+    uint64_t aborts;           /* aborted attempts (abort rate = aborts/committed) */
+    uint64_t timeouts;
+    uint64_t invalid;
+    uint64_t max_attempts;     /* largest attempts count of any transaction */
+    uint32_t device_error;     /* GCC_DEVERR_* bits */
+    uint32_t scheme;
+    double elapsed_ms;         /* device time of the batch (submit/wait only) */
+} gcc_batch_stats;
+
+/* device_error bits */
+#define GCC_DEVERR_WAIT_BUDGET   0x1u   /* a deterministic wait ran out        */
+#define GCC_DEVERR_DEADLINE      0x2u   /* deadline_ns passed                  */
+#define GCC_DEVERR_TS_OVERFLOW   0x4u   /* timestamp ordering ran past 2^31-1  */
+#define GCC_DEVERR_ATTEMPTS      0x8u   /* a transaction hit max_attempts      */
+#define GCC_DEVERR_INVALID       0x10u  /* a transaction was malformed         */
+#define GCC_DEVERR_INSERT        0x20u  /* an order insert had no free slot    */
+
+typedef struct gcc_db gcc_db;
+typedef struct gcc_batch gcc_batch;
+
+/* Create a database on desc->device: allocates its tables (zeroed), the
+ * per-record concurrency-control words and the scratch needed for batches
+ * up to the stated maxima.  Key-value: one table (id 0).  Order-entry: one
+ * table per column (ids 0..21 in this order: w_ytd, w_tax, d_ytd, d_tax,
+ * d_next_o_id, c_balance, c_ytd_payment, c_payment_cnt, c_discount, i_price,
+ * s_quantity, s_ytd, s_order_cnt, s_remote_cnt, o_c_id, o_ol_cnt,
+ * o_all_local, no_flag, ol_i_id, ol_supply_w_id, ol_quantity, ol_amount; all
+ * int64; order slot = district * order_cap + o_id - 1, line = slot * 15 + l).
+ * Errors: GCC_ERR_INVALID (desc out of range), GCC_ERR_NOMEM, GCC_ERR_CUDA. */
+gcc_status gcc_db_create(const gcc_db_desc *desc, gcc_db **out);
+
+/* Free every device allocation of db (synchronises its stream).  NULL is a
+ * no-op. */
+gcc_status gcc_db_destroy(gcc_db *db);
+
+/* Number of tables and the byte size of one table (0 for a bad id). */
+uint32_t gcc_table_count(const gcc_db *db);
+uint64_t gcc_table_bytes(const gcc_db *db, uint32_t table_id);
+
+/* Copy nbytes (must equal gcc_table_bytes) into table table_id from a host
+ * (src_on_device = 0) or device pointer, and reset the concurrency-control
+ * words.  Synchronous.  Key-value layout: field-major, slot (key, field) at
+ * byte (field * n_records + key) * field_bytes. */
+gcc_status gcc_load_table(gcc_db *db, uint32_t table_id, const void *src,
+                          uint64_t nbytes, int src_on_device);
+
+/* Copy table table_id out (synchronous; waits for prior work on the stream). */
+gcc_status gcc_db_read_table(gcc_db *db, uint32_t table_id, void *dst,
+                             uint64_t nbytes, int dst_on_device);
+
+/* Fill *p with the defaults. */
+gcc_status gcc_default_params(gcc_exec_params *p);
+
+/* Submit a batch asynchronously.  txns/ops/operands are host pointers
+ * (copied before the call returns) or, with inputs_on_device = 1, device
+ * pointers that must stay valid until gcc_batch_wait returns.  params may be
+ * NULL (defaults).  stream: a cudaStream_t, or NULL for the database's own
+ * stream.  Errors: GCC_ERR_INVALID (n_ops/op ranges inconsistent, bad
+ * scheme), GCC_ERR_CAPACITY (beyond the create-time maxima), GCC_ERR_NOMEM,
+ * GCC_ERR_CUDA.  Per-transaction problems (bad keys, duplicates) are not
+ * errors here: those transactions come back as GCC_TXN_INVALID. */
+gcc_status gcc_txn_batch_submit(gcc_db *db, gcc_scheme scheme, const gcc_txn *txns,
+                                uint32_t n_txns, const gcc_op *ops,
+                                const gcc_operand *operands, uint64_t n_ops,
+                                int inputs_on_device, const gcc_exec_params *params,
+                                void *stream, gcc_batch **out);
+
+/* Wait up to timeout_ns (UINT64_MAX = forever) for the batch, then copy its
+ * per-transaction results (n_txns entries) and read values (n_ops entries,
+ * indexed like ops) to host (outputs_on_device = 0) or device pointers; any
+ * output pointer may be NULL.  GCC_ERR_TIMEOUT leaves the batch waitable
+ * again.  GCC_ERR_DEVICE when stats.device_error is nonzero (outputs are
+ * still written). */
+gcc_status gcc_batch_wait(gcc_batch *batch, uint64_t timeout_ns, gcc_txn_result *results,
+                          gcc_operand *read_values, gcc_batch_stats *stats,
+                          int outputs_on_device);
+
+/* Release a batch (waits for it first).  NULL is a no-op. */
+gcc_status gcc_batch_free(gcc_batch *batch);
+
+/* Device-resident form of submit: every pointer is a device pointer, the
+ * results are written to d_results (n_txns) and d_reads (n_ops), and the
+ * call only enqueues work on `stream` (NULL = the database's stream).  No
+ * allocation happens here.  Statistics of the latest execution are read
+ * with gcc_last_stats. */
+gcc_status gcc_execute(gcc_db *db, gcc_scheme scheme, const gcc_txn *d_txns,
+                       uint32_t n_txns, const gcc_op *d_ops,
+                       const gcc_operand *d_operands, uint64_t n_ops,
+                       const gcc_exec_params *params, gcc_txn_result *d_results,
+                       gcc_operand *d_reads, void *stream);
+
+/* Statistics of the latest gcc_execute / submit on db (synchronises its
+ * stream; elapsed_ms is 0 for gcc_execute). */
+gcc_status gcc_last_stats(gcc_db *db, gcc_batch_stats *stats);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *gcc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GCC_GB300_H */

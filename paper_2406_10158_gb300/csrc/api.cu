@@ -1,0 +1,577 @@
+// api.cu -- host runtime behind the C ABI in include/gcc_gb300.h.
+//
+// Owns the database's device memory (tables, one concurrency-control word per
+// record, batch scratch), decides when the control words must be reset
+// between batches, sizes the persistent grid from the occupancy of the
+// chosen kernel, and runs a batch as a stream-ordered sequence:
+//   batch-begin -> [deterministic: access table, sort, thresholds]
+//   -> execute kernel -> [OCC/TO: dense commit ranks].
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+
+#include "engine.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+gcc_status fail(gcc_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define GCC_CK(call)                                                                   \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(e_ == cudaErrorMemoryAllocation ? GCC_ERR_NOMEM : GCC_ERR_CUDA, \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));               \
+    } while (0)
+
+constexpr int OE_NCOLS = 22;
+constexpr uint32_t OE_ITEMS = 100000, OE_DIST = 10, OE_CUST = 3000, OE_LINES = 15;
+
+// Rows of each order-entry column, in table-id order.
+uint64_t oe_rows(uint32_t col, uint64_t W, uint64_t cap) {
+    const uint64_t nd = W * OE_DIST;
+    if (col < 2) return W;                          // w_ytd, w_tax
+    if (col < 5) return nd;                         // d_ytd, d_tax, d_next_o_id
+    if (col < 9) return nd * OE_CUST;               // c_*
+    if (col < 10) return OE_ITEMS;                  // i_price
+    if (col < 14) return W * OE_ITEMS;              // s_*
+    if (col < 18) return nd * cap;                  // o_*, no_flag
+    return nd * cap * OE_LINES;                     // ol_*
+}
+
+enum MetaState { META_ZERO, META_OCC, META_TO, META_DET, META_UNKNOWN };
+
+}  // namespace
+
+struct gcc_db {
+    gcc_db_desc d{};
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    // key-value
+    uint8_t* table = nullptr;
+    uint64_t table_bytes = 0;
+    // order-entry
+    int64_t* cols[OE_NCOLS] = {};
+    uint64_t col_bytes[OE_NCOLS] = {};
+    int64_t** d_cols = nullptr;
+    // concurrency control
+    uint64_t* meta = nullptr;
+    uint64_t n_meta = 0;
+    gcc::BatchState* st = nullptr;
+    gcc::DbState* dbs = nullptr;
+    MetaState meta_state = META_ZERO;
+    // scratch
+    gcc::SortScratch sort{};
+    uint32_t* scan_tmp = nullptr;
+    uint32_t* need = nullptr;
+    unsigned long long* order_key = nullptr;
+    // latest execution
+    cudaStream_t last_stream = nullptr;
+    gcc_scheme last_scheme = GCC_OCC;
+    uint64_t last_n_txns = 0;
+    // pinned copies of BatchState for submitted batches
+    gcc::BatchState* h_states = nullptr;
+    uint32_t n_h_states = 0, next_h_state = 0;
+};
+
+struct gcc_batch {
+    gcc_db* db = nullptr;
+    cudaStream_t stream = nullptr;
+    gcc_scheme scheme = GCC_OCC;
+    uint32_t n_txns = 0;
+    uint64_t n_ops = 0;
+    void* d_in = nullptr;                 // staged inputs (host-input batches)
+    gcc_txn_result* d_results = nullptr;
+    gcc_operand* d_reads = nullptr;
+    gcc::BatchState* h_state = nullptr;   // pinned, filled at batch end
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+};
+
+namespace {
+
+gcc_exec_params defaults() {
+    gcc_exec_params p{};
+    p.lanes_per_txn = 16;
+    p.warps_per_block = 8;
+    p.blocks_per_sm = 0;
+    p.collapse = 1;
+    p.backoff_base_ns = 0;
+    p.backoff_cap_ns = 100000;
+    p.max_attempts = 1u << 24;
+    p.read_retries = 8;
+    p.wait_budget_ns = 2000000000ull;
+    p.deadline_ns = 60000000000ull;
+    p.seed = 0x5EEDull;
+    p.inject_abort_ppm = 0;
+    return p;
+}
+
+gcc_exec_params merged(const gcc_exec_params* in) {
+    gcc_exec_params p = defaults();
+    if (!in) return p;
+    if (in->lanes_per_txn) p.lanes_per_txn = in->lanes_per_txn;
+    if (in->warps_per_block) p.warps_per_block = in->warps_per_block;
+    p.blocks_per_sm = in->blocks_per_sm;
+    if (in->collapse) p.collapse = in->collapse;
+    p.backoff_base_ns = in->backoff_base_ns;
+    if (in->backoff_cap_ns) p.backoff_cap_ns = in->backoff_cap_ns;
+    if (in->max_attempts) p.max_attempts = in->max_attempts;
+    if (in->read_retries) p.read_retries = in->read_retries;
+    if (in->wait_budget_ns) p.wait_budget_ns = in->wait_budget_ns;
+    if (in->deadline_ns) p.deadline_ns = in->deadline_ns;
+    if (in->seed) p.seed = in->seed;
+    p.inject_abort_ppm = in->inject_abort_ppm;
+    return p;
+}
+
+int bit_length(uint64_t v) {
+    int b = 0;
+    while (v) { ++b; v >>= 1; }
+    return b;
+}
+
+template <class T>
+gcc_status dev_alloc(T** p, uint64_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) return GCC_OK;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(GCC_ERR_NOMEM, "cudaMalloc of %llu bytes for %s failed: %s",
+                    (unsigned long long)bytes, what, cudaGetErrorString(e));
+    }
+    e = cudaMemset(*p, 0, bytes);
+    if (e != cudaSuccess) return fail(GCC_ERR_CUDA, "cudaMemset: %s", cudaGetErrorString(e));
+    return GCC_OK;
+}
+
+void free_db(gcc_db* db) {
+    cudaSetDevice(db->d.device);
+    if (db->stream) cudaStreamSynchronize(db->stream);
+    cudaFree(db->table);
+    for (auto& c : db->cols) cudaFree(c);
+    cudaFree(db->d_cols);
+    cudaFree(db->meta);
+    cudaFree(db->st);
+    cudaFree(db->dbs);
+    cudaFree(db->sort.k0);
+    cudaFree(db->sort.v0);
+    cudaFree(db->sort.k1);
+    cudaFree(db->sort.v1);
+    cudaFree(db->sort.hist);
+    cudaFree(db->sort.totals);
+    cudaFree(db->scan_tmp);
+    cudaFree(db->need);
+    cudaFree(db->order_key);
+    if (db->h_states) cudaFreeHost(db->h_states);
+    if (db->stream) cudaStreamDestroy(db->stream);
+    delete db;
+}
+
+gcc_status create_impl(const gcc_db_desc* desc, gcc_db** out) {
+    if (!desc || !out) return fail(GCC_ERR_INVALID, "null argument");
+    *out = nullptr;
+    const gcc_db_desc& d = *desc;
+    if (d.schema == GCC_SCHEMA_KV) {
+        if (d.field_bytes != 8 && d.field_bytes != 16)
+            return fail(GCC_ERR_INVALID, "field_bytes must be 8 or 16");
+        if (d.n_records == 0 || d.n_records > (1ull << 31))
+            return fail(GCC_ERR_INVALID, "n_records must be in 1..2^31");
+        if (d.n_fields == 0 || d.n_fields > 255)
+            return fail(GCC_ERR_INVALID, "n_fields must be in 1..255");
+    } else if (d.schema == GCC_SCHEMA_ORDER_ENTRY) {
+        if (d.n_warehouses == 0 || d.n_warehouses > 1024)
+            return fail(GCC_ERR_INVALID, "n_warehouses must be in 1..1024");
+        if (d.order_cap < 3000 || d.order_cap > (1u << 24))
+            return fail(GCC_ERR_INVALID, "order_cap must be in 3000..2^24");
+    } else {
+        return fail(GCC_ERR_INVALID, "unknown schema %u", d.schema);
+    }
+    if (d.max_ops_per_txn == 0 || d.max_ops_per_txn > 64)
+        return fail(GCC_ERR_INVALID, "max_ops_per_txn must be in 1..64");
+    if (d.max_batch_txns == 0 || d.max_batch_txns > (1ull << 31))
+        return fail(GCC_ERR_INVALID, "max_batch_txns must be in 1..2^31");
+    if (d.max_batch_ops == 0 || d.max_batch_ops >= (1ull << 32))
+        return fail(GCC_ERR_INVALID, "max_batch_ops must be in 1..2^32-1");
+    int ndev = 0;
+    GCC_CK(cudaGetDeviceCount(&ndev));
+    if (d.device < 0 || d.device >= ndev) return fail(GCC_ERR_INVALID, "no CUDA device %d", d.device);
+    GCC_CK(cudaSetDevice(d.device));
+
+    gcc_db* db = new (std::nothrow) gcc_db();
+    if (!db) return fail(GCC_ERR_NOMEM, "host allocation failed");
+    db->d = d;
+    gcc_status s = GCC_OK;
+    auto bail = [&](gcc_status st) { free_db(db); return st; };
+    if (cudaDeviceGetAttribute(&db->sm_count, cudaDevAttrMultiProcessorCount, d.device) != cudaSuccess)
+        return bail(fail(GCC_ERR_CUDA, "cannot query SM count"));
+    if (cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(GCC_ERR_CUDA, "cannot create stream"));
+
+    if (d.schema == GCC_SCHEMA_KV) {
+        db->table_bytes = d.n_records * d.n_fields * d.field_bytes;
+        if ((s = dev_alloc(&db->table, db->table_bytes, "table"))) return bail(s);
+        db->n_meta = d.n_records;
+    } else {
+        const uint64_t W = d.n_warehouses;
+        for (int c = 0; c < OE_NCOLS; ++c) {
+            db->col_bytes[c] = oe_rows(c, W, d.order_cap) * sizeof(int64_t);
+            if ((s = dev_alloc(&db->cols[c], db->col_bytes[c], "order-entry column"))) return bail(s);
+        }
+        if ((s = dev_alloc(&db->d_cols, sizeof(int64_t*) * OE_NCOLS, "column table"))) return bail(s);
+        if (cudaMemcpy(db->d_cols, db->cols, sizeof(int64_t*) * OE_NCOLS, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return bail(fail(GCC_ERR_CUDA, "cannot upload column table"));
+        db->n_meta = W * (1 + OE_DIST + OE_DIST * OE_CUST) + W * OE_ITEMS;
+    }
+    if ((s = dev_alloc(&db->meta, db->n_meta * 8, "control words"))) return bail(s);
+    if ((s = dev_alloc(&db->st, sizeof(gcc::BatchState), "batch state"))) return bail(s);
+    if ((s = dev_alloc(&db->dbs, sizeof(gcc::DbState), "db state"))) return bail(s);
+    const uint64_t items = std::max<uint64_t>(d.max_batch_ops, d.max_batch_txns);
+    db->sort.max_items = items;
+    if ((s = dev_alloc(&db->sort.k0, items * 4, "sort keys"))) return bail(s);
+    if ((s = dev_alloc(&db->sort.v0, items * 4, "sort values"))) return bail(s);
+    if ((s = dev_alloc(&db->sort.k1, items * 4, "sort keys"))) return bail(s);
+    if ((s = dev_alloc(&db->sort.v1, items * 4, "sort values"))) return bail(s);
+    if ((s = dev_alloc(&db->sort.hist, gcc::sort_max_tiles(items) * 256 * 4, "sort histogram")))
+        return bail(s);
+    if ((s = dev_alloc(&db->sort.totals, 256 * 4, "sort totals"))) return bail(s);
+    if ((s = dev_alloc(&db->scan_tmp, gcc::scan_tmp_words(items) * 4, "scan scratch"))) return bail(s);
+    if ((s = dev_alloc(&db->need, d.max_batch_ops * 4, "wait thresholds"))) return bail(s);
+    if ((s = dev_alloc(&db->order_key, d.max_batch_txns * 8, "commit keys"))) return bail(s);
+    db->n_h_states = 256;
+    if (cudaMallocHost(&db->h_states, sizeof(gcc::BatchState) * db->n_h_states) != cudaSuccess)
+        return bail(fail(GCC_ERR_NOMEM, "cannot allocate pinned batch states"));
+    *out = db;
+    return GCC_OK;
+}
+
+gcc_status validate_params(const gcc_exec_params& p) {
+    const uint32_t g = p.lanes_per_txn;
+    if (g == 0 || g > 32 || (g & (g - 1)))
+        return fail(GCC_ERR_INVALID, "lanes_per_txn must be a power of two in 1..32");
+    if (p.warps_per_block == 0 || p.warps_per_block > 32)
+        return fail(GCC_ERR_INVALID, "warps_per_block must be in 1..32");
+    if (p.collapse > 2) return fail(GCC_ERR_INVALID, "collapse must be 0, 1 or 2");
+    return GCC_OK;
+}
+
+gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, uint32_t n_txns,
+                        const gcc_op* d_ops, const gcc_operand* d_operands, uint64_t n_ops,
+                        const gcc_exec_params* params, gcc_txn_result* d_results,
+                        gcc_operand* d_reads, cudaStream_t stream) {
+    if (!db) return fail(GCC_ERR_INVALID, "null database");
+    if ((unsigned)scheme > GCC_DET) return fail(GCC_ERR_INVALID, "unknown scheme %d", (int)scheme);
+    if (n_txns > db->d.max_batch_txns || n_ops > db->d.max_batch_ops)
+        return fail(GCC_ERR_CAPACITY, "batch of %u txns / %llu ops exceeds the database maxima",
+                    n_txns, (unsigned long long)n_ops);
+    if (n_txns && (!d_txns || !d_results)) return fail(GCC_ERR_INVALID, "null batch pointer");
+    if (n_ops && (!d_ops || !d_operands || !d_reads)) return fail(GCC_ERR_INVALID, "null op pointer");
+    gcc_exec_params p = merged(params);
+    gcc_status s = validate_params(p);
+    if (s) return s;
+    GCC_CK(cudaSetDevice(db->d.device));
+    cudaStream_t st = stream ? stream : db->stream;
+
+    // control words: reset whenever the previous batch left them in a state
+    // the scheme cannot start from
+    bool reset = false;
+    switch (scheme) {
+        case GCC_NO_WAIT_2PL: reset = db->meta_state != META_ZERO; break;
+        case GCC_OCC: reset = db->meta_state != META_ZERO && db->meta_state != META_OCC; break;
+        case GCC_TO: reset = true; break;      // timestamps are per batch
+        case GCC_DET: reset = false; break;    // per-record counters set by preprocessing
+    }
+    if (reset) GCC_CK(cudaMemsetAsync(db->meta, 0, db->n_meta * 8, st));
+
+    gcc::ExecArgs a{};
+    a.txns = d_txns;
+    a.ops = reinterpret_cast<const uint64_t*>(d_ops);
+    a.operands = reinterpret_cast<const ulonglong2*>(d_operands);
+    a.n_txns = n_txns;
+    a.n_ops = n_ops;
+    a.results = d_results;
+    a.reads = reinterpret_cast<ulonglong2*>(d_reads);
+    a.table = db->table;
+    a.n_records = db->d.n_records;
+    a.n_fields = db->d.n_fields;
+    a.meta = db->meta;
+    a.n_meta = db->n_meta;
+    a.cols = db->d_cols;
+    a.n_warehouses = db->d.n_warehouses;
+    a.order_cap = db->d.order_cap;
+    a.need = db->need;
+    a.order_key = db->order_key;
+    a.order_key_uses_base = scheme == GCC_OCC;
+    a.st = db->st;
+    a.dbs = db->dbs;
+    a.lanes = p.lanes_per_txn;
+    a.max_ops = db->d.max_ops_per_txn;
+    a.collapse = p.collapse;
+    a.backoff_base_ns = p.backoff_base_ns;
+    a.backoff_cap_ns = p.backoff_cap_ns;
+    a.max_attempts = p.max_attempts;
+    a.read_retries = p.read_retries;
+    a.inject_ppm = p.inject_abort_ppm;
+    a.wait_budget_ns = p.wait_budget_ns;
+    a.deadline_ns = p.deadline_ns;
+    a.seed = p.seed;
+
+    GCC_CK(gcc::launch_batch_begin(db->st, db->dbs, scheme, st));
+    const bool kv = db->d.schema == GCC_SCHEMA_KV;
+    if (scheme == GCC_DET) {
+        const int bits = kv ? bit_length(db->n_meta - 1) : bit_length(db->n_meta);
+        GCC_CK(gcc::det_prepare(a, db->sort, db->scan_tmp, std::max(bits, 1), db->d.schema, st));
+    }
+    const int block = (int)p.warps_per_block * 32;
+    const uint32_t slots = block / p.lanes_per_txn;
+    const size_t smem = (size_t)slots * db->d.max_ops_per_txn * gcc::STAGE_BYTES_PER_OP;
+    const int occ = kv ? gcc::kv_exec_occupancy(scheme, db->d.field_bytes, block, smem)
+                       : gcc::oe_exec_occupancy(scheme, block, smem);
+    if (occ <= 0)
+        return fail(GCC_ERR_INVALID, "launch shape does not fit an SM (%d threads, %zu B shared)",
+                    block, smem);
+    int per_sm = p.blocks_per_sm ? std::min<int>(p.blocks_per_sm, occ) : occ;
+    int64_t grid = (int64_t)db->sm_count * per_sm;
+    const int64_t needed = ((int64_t)n_txns + slots - 1) / slots;
+    grid = std::max<int64_t>(1, std::min(grid, needed));
+    if (n_txns) {
+        GCC_CK(kv ? gcc::launch_kv_exec(scheme, db->d.field_bytes, a, (int)grid, block, smem, st)
+                  : gcc::launch_oe_exec(scheme, a, (int)grid, block, smem, st));
+        if (scheme == GCC_OCC || scheme == GCC_TO)
+            GCC_CK(gcc::densify_commit_order(a, db->sort, st));
+    }
+    switch (scheme) {
+        case GCC_NO_WAIT_2PL: db->meta_state = META_ZERO; break;
+        case GCC_OCC: db->meta_state = META_OCC; break;
+        case GCC_TO: db->meta_state = META_TO; break;
+        case GCC_DET: db->meta_state = META_DET; break;
+    }
+    db->last_stream = st;
+    db->last_scheme = scheme;
+    db->last_n_txns = n_txns;
+    return GCC_OK;
+}
+
+void fill_stats(const gcc::BatchState& h, gcc_scheme scheme, uint64_t n_txns, gcc_batch_stats* s) {
+    s->n_txns = n_txns;
+    s->committed = h.committed;
+    s->aborts = h.aborts;
+    s->timeouts = h.timeouts;
+    s->invalid = h.invalid;
+    s->max_attempts = h.max_attempts;
+    s->device_error = h.error;
+    s->scheme = scheme;
+    s->elapsed_ms = 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gcc_last_error(void) { return g_err.c_str(); }
+
+gcc_status gcc_default_params(gcc_exec_params* p) {
+    if (!p) return fail(GCC_ERR_INVALID, "null params");
+    *p = defaults();
+    return GCC_OK;
+}
+
+gcc_status gcc_db_create(const gcc_db_desc* desc, gcc_db** out) { return create_impl(desc, out); }
+
+gcc_status gcc_db_destroy(gcc_db* db) {
+    if (db) free_db(db);
+    return GCC_OK;
+}
+
+uint32_t gcc_table_count(const gcc_db* db) {
+    if (!db) return 0;
+    return db->d.schema == GCC_SCHEMA_KV ? 1u : (uint32_t)OE_NCOLS;
+}
+
+uint64_t gcc_table_bytes(const gcc_db* db, uint32_t id) {
+    if (!db) return 0;
+    if (db->d.schema == GCC_SCHEMA_KV) return id == 0 ? db->table_bytes : 0;
+    return id < (uint32_t)OE_NCOLS ? db->col_bytes[id] : 0;
+}
+
+static void* table_ptr(gcc_db* db, uint32_t id) {
+    return db->d.schema == GCC_SCHEMA_KV ? (void*)db->table : (void*)db->cols[id];
+}
+
+gcc_status gcc_load_table(gcc_db* db, uint32_t id, const void* src, uint64_t nbytes,
+                          int src_on_device) {
+    if (!db || !src) return fail(GCC_ERR_INVALID, "null argument");
+    const uint64_t want = gcc_table_bytes(db, id);
+    if (want == 0) return fail(GCC_ERR_INVALID, "no table %u", id);
+    if (nbytes != want)
+        return fail(GCC_ERR_INVALID, "table %u holds %llu bytes, got %llu", id,
+                    (unsigned long long)want, (unsigned long long)nbytes);
+    GCC_CK(cudaSetDevice(db->d.device));
+    GCC_CK(cudaDeviceSynchronize());
+    GCC_CK(cudaMemcpy(table_ptr(db, id), src, nbytes,
+                      src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    GCC_CK(cudaMemset(db->meta, 0, db->n_meta * 8));
+    db->meta_state = META_ZERO;
+    GCC_CK(cudaDeviceSynchronize());
+    return GCC_OK;
+}
+
+gcc_status gcc_db_read_table(gcc_db* db, uint32_t id, void* dst, uint64_t nbytes,
+                             int dst_on_device) {
+    if (!db || !dst) return fail(GCC_ERR_INVALID, "null argument");
+    const uint64_t want = gcc_table_bytes(db, id);
+    if (want == 0) return fail(GCC_ERR_INVALID, "no table %u", id);
+    if (nbytes != want)
+        return fail(GCC_ERR_INVALID, "table %u holds %llu bytes, got %llu", id,
+                    (unsigned long long)want, (unsigned long long)nbytes);
+    GCC_CK(cudaSetDevice(db->d.device));
+    GCC_CK(cudaDeviceSynchronize());
+    GCC_CK(cudaMemcpy(dst, table_ptr(db, id), nbytes,
+                      dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    return GCC_OK;
+}
+
+gcc_status gcc_execute(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, uint32_t n_txns,
+                       const gcc_op* d_ops, const gcc_operand* d_operands, uint64_t n_ops,
+                       const gcc_exec_params* params, gcc_txn_result* d_results,
+                       gcc_operand* d_reads, void* stream) {
+    return execute_impl(db, scheme, d_txns, n_txns, d_ops, d_operands, n_ops, params, d_results,
+                        d_reads, static_cast<cudaStream_t>(stream));
+}
+
+gcc_status gcc_last_stats(gcc_db* db, gcc_batch_stats* stats) {
+    if (!db || !stats) return fail(GCC_ERR_INVALID, "null argument");
+    GCC_CK(cudaSetDevice(db->d.device));
+    gcc::BatchState h{};
+    GCC_CK(cudaStreamSynchronize(db->last_stream ? db->last_stream : db->stream));
+    GCC_CK(cudaMemcpy(&h, db->st, sizeof h, cudaMemcpyDeviceToHost));
+    fill_stats(h, db->last_scheme, db->last_n_txns, stats);
+    return GCC_OK;
+}
+
+gcc_status gcc_txn_batch_submit(gcc_db* db, gcc_scheme scheme, const gcc_txn* txns,
+                                uint32_t n_txns, const gcc_op* ops, const gcc_operand* operands,
+                                uint64_t n_ops, int inputs_on_device,
+                                const gcc_exec_params* params, void* stream, gcc_batch** out) {
+    if (!db || !out) return fail(GCC_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (n_txns > db->d.max_batch_txns || n_ops > db->d.max_batch_ops)
+        return fail(GCC_ERR_CAPACITY, "batch exceeds the database maxima");
+    GCC_CK(cudaSetDevice(db->d.device));
+    gcc_batch* b = new (std::nothrow) gcc_batch();
+    if (!b) return fail(GCC_ERR_NOMEM, "host allocation failed");
+    b->db = db;
+    b->stream = stream ? static_cast<cudaStream_t>(stream) : db->stream;
+    b->scheme = scheme;
+    b->n_txns = n_txns;
+    b->n_ops = n_ops;
+    b->h_state = &db->h_states[db->next_h_state++ % db->n_h_states];
+    auto bail = [&](gcc_status s) {
+        gcc_batch_free(b);
+        return s;
+    };
+    if (cudaEventCreate(&b->ev_start) != cudaSuccess || cudaEventCreate(&b->ev_done) != cudaSuccess)
+        return bail(fail(GCC_ERR_CUDA, "cannot create events"));
+    const uint64_t tb = (uint64_t)n_txns * sizeof(gcc_txn), ob = n_ops * sizeof(gcc_op),
+                   pb = n_ops * sizeof(gcc_operand);
+    const gcc_txn* d_txns = txns;
+    const gcc_op* d_ops = ops;
+    const gcc_operand* d_operands = operands;
+    cudaError_t e;
+    if (!inputs_on_device && (tb + ob + pb) > 0) {
+        const uint64_t pad = 256;
+        e = cudaMallocAsync(&b->d_in, tb + ob + pb + 3 * pad, b->stream);
+        if (e != cudaSuccess) return bail(fail(GCC_ERR_NOMEM, "input staging: %s", cudaGetErrorString(e)));
+        char* base = static_cast<char*>(b->d_in);
+        char* pt = base;
+        char* po = base + ((tb + pad - 1) / pad) * pad;
+        char* pp = po + ((ob + pad - 1) / pad) * pad;
+        if ((tb && cudaMemcpyAsync(pt, txns, tb, cudaMemcpyHostToDevice, b->stream)) ||
+            (ob && cudaMemcpyAsync(po, ops, ob, cudaMemcpyHostToDevice, b->stream)) ||
+            (pb && cudaMemcpyAsync(pp, operands, pb, cudaMemcpyHostToDevice, b->stream)))
+            return bail(fail(GCC_ERR_CUDA, "input upload failed"));
+        d_txns = reinterpret_cast<const gcc_txn*>(pt);
+        d_ops = reinterpret_cast<const gcc_op*>(po);
+        d_operands = reinterpret_cast<const gcc_operand*>(pp);
+    }
+    if (n_txns && cudaMallocAsync(&b->d_results, (uint64_t)n_txns * sizeof(gcc_txn_result), b->stream))
+        return bail(fail(GCC_ERR_NOMEM, "result buffer"));
+    if (n_ops && cudaMallocAsync(&b->d_reads, n_ops * sizeof(gcc_operand), b->stream))
+        return bail(fail(GCC_ERR_NOMEM, "read-value buffer"));
+    if (cudaEventRecord(b->ev_start, b->stream)) return bail(fail(GCC_ERR_CUDA, "event record"));
+    gcc_status s = execute_impl(db, scheme, d_txns, n_txns, d_ops, d_operands, n_ops, params,
+                                b->d_results, b->d_reads, b->stream);
+    if (s) return bail(s);
+    if (cudaMemcpyAsync(b->h_state, db->st, sizeof(gcc::BatchState), cudaMemcpyDeviceToHost,
+                        b->stream) ||
+        cudaEventRecord(b->ev_done, b->stream))
+        return bail(fail(GCC_ERR_CUDA, "batch completion record"));
+    *out = b;
+    return GCC_OK;
+}
+
+gcc_status gcc_batch_wait(gcc_batch* b, uint64_t timeout_ns, gcc_txn_result* results,
+                          gcc_operand* read_values, gcc_batch_stats* stats, int outputs_on_device) {
+    if (!b) return fail(GCC_ERR_INVALID, "null batch");
+    GCC_CK(cudaSetDevice(b->db->d.device));
+    const auto t0 = std::chrono::steady_clock::now();
+    for (uint32_t spin = 0;; ++spin) {
+        cudaError_t q = cudaEventQuery(b->ev_done);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return fail(GCC_ERR_CUDA, "batch failed: %s", cudaGetErrorString(q));
+        const uint64_t waited = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                    std::chrono::steady_clock::now() - t0).count();
+        if (timeout_ns != UINT64_MAX && waited >= timeout_ns)
+            return fail(GCC_ERR_TIMEOUT, "batch still running after %llu ns",
+                        (unsigned long long)waited);
+        if (spin > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    const cudaMemcpyKind k = outputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (results && b->n_txns)
+        GCC_CK(cudaMemcpyAsync(results, b->d_results, (uint64_t)b->n_txns * sizeof(gcc_txn_result), k,
+                               b->stream));
+    if (read_values && b->n_ops)
+        GCC_CK(cudaMemcpyAsync(read_values, b->d_reads, b->n_ops * sizeof(gcc_operand), k, b->stream));
+    GCC_CK(cudaStreamSynchronize(b->stream));
+    gcc::BatchState h = *b->h_state;
+    if (stats) {
+        fill_stats(h, b->scheme, b->n_txns, stats);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, b->ev_start, b->ev_done) == cudaSuccess) stats->elapsed_ms = ms;
+    }
+    if (h.error) return fail(GCC_ERR_DEVICE, "device reported error flags 0x%x", h.error);
+    return GCC_OK;
+}
+
+gcc_status gcc_batch_free(gcc_batch* b) {
+    if (!b) return GCC_OK;
+    cudaSetDevice(b->db->d.device);
+    if (b->ev_done) cudaEventSynchronize(b->ev_done);
+    else cudaStreamSynchronize(b->stream);
+    if (b->d_in) cudaFreeAsync(b->d_in, b->stream);
+    if (b->d_results) cudaFreeAsync(b->d_results, b->stream);
+    if (b->d_reads) cudaFreeAsync(b->d_reads, b->stream);
+    if (b->ev_start) cudaEventDestroy(b->ev_start);
+    if (b->ev_done) cudaEventDestroy(b->ev_done);
+    delete b;
+    return GCC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,244 @@
+// engine.cuh -- internal declarations of the concurrency-control engine.
+//
+// Memory-ordering primitives, the per-batch device state, kernel argument
+// blocks and the host-side launch entry points shared by the translation
+// units of the library.  Not part of the public ABI (include/gcc_gb300.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gcc_gb300.h"
+
+namespace gcc {
+
+// ---------------------------------------------------------------------------
+// concurrency-control word layouts (one 64-bit word per record, Table II)
+// ---------------------------------------------------------------------------
+// OCC: bit 63 lock, bits 0..62 version = commit timestamp + 1 (Sec. III-E.2,
+// "lock bit : 1, ts : 63").
+constexpr uint64_t OCC_LOCK = 1ull << 63;
+// 2PL: bit 63 exclusive, bits 32..62 shared-holder count, bits 0..31 exclusive
+// holder (transaction id + 1) -- Table II's shared bit / holder count / holder.
+constexpr uint64_t TPL_X = 1ull << 63;
+constexpr uint64_t TPL_S_ONE = 1ull << 32;
+// TO: bit 63 dirty (the commit bit of Table II), bits 31..61 RTS, bits 0..30 WTS.
+constexpr uint64_t TO_DIRTY = 1ull << 63;
+constexpr uint64_t TO_TS_MASK = (1ull << 31) - 1;
+constexpr int TO_RTS_SHIFT = 31;
+// DET: bits 32..63 ops completed on the record, bits 0..31 writes completed,
+// both counted from the record's first position in the batch's sorted
+// access table (Sec. III-E.3, "access tables").
+constexpr uint64_t DET_READ_DONE = 1ull << 32;
+constexpr uint64_t DET_WRITE_DONE = (1ull << 32) + 1;
+
+// Per-batch device state (zeroed by the batch-begin kernel).
+struct BatchState {
+    unsigned long long fetch;        // next transaction id to hand out
+    unsigned long long ticket;       // 2PL commit counter / TO timestamp counter
+    unsigned long long ticket_base;  // OCC: persistent clock at batch start
+    unsigned long long committed;
+    unsigned long long aborts;
+    unsigned long long timeouts;
+    unsigned long long invalid;
+    unsigned long long max_attempts;
+    unsigned int error;              // GCC_DEVERR_* bits
+    unsigned int pad;
+};
+
+// Persistent per-database device state.
+struct DbState {
+    unsigned long long occ_clock;    // OCC commit timestamps, never reset
+};
+
+// ---------------------------------------------------------------------------
+// PTX memory-order helpers (gpu scope)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// 16-byte record slot access (one vector transaction).
+__device__ __forceinline__ ulonglong2 ld_slot16(const void* p) {
+    ulonglong2 v;
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];"
+                 : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_slot16(void* p, ulonglong2 v) {
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};"
+                 ::"l"(p), "l"(v.x), "l"(v.y) : "memory");
+}
+__device__ __forceinline__ uint64_t cas64(uint64_t* p, uint64_t cmp, uint64_t val) {
+    return atomicCAS(reinterpret_cast<unsigned long long*>(p), cmp, val);
+}
+__device__ __forceinline__ uint64_t add64(uint64_t* p, uint64_t v) {
+    return atomicAdd(reinterpret_cast<unsigned long long*>(p), v);
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// One ticket from a counter per calling lane, with one atomic per warp:
+// the lanes active at the call share a single atomicAdd.
+__device__ __forceinline__ unsigned long long agg_ticket(unsigned long long* ctr) {
+    unsigned mask = __activemask();
+    int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if ((threadIdx.x & 31) == leader) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + __popc(mask & lanemask_lt());
+}
+
+// 64-bit mixing (splitmix64 finaliser) for jitter and abort injection.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z ^= z >> 30; z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27; z *= 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Op kinds that modify their record (the deterministic scheme's writers).
+__host__ __device__ __forceinline__ bool kind_writes(uint32_t kind) {
+    switch (kind) {
+        case GCC_OP_ADD:
+        case GCC_OE_W_PAY:
+        case GCC_OE_D_NEWORDER:
+        case GCC_OE_D_PAY:
+        case GCC_OE_C_PAY:
+        case GCC_OE_S_NEWORDER:
+            return true;
+        default:
+            return false;
+    }
+}
+
+// Concurrency-control record of an op: the key itself for key-value tables;
+// for order-entry, the row offset by its table's base in the record space
+// (warehouse, district, customer, stock).  Item reads need no control and
+// map to `none`.
+__host__ __device__ __forceinline__ uint32_t cc_record(uint64_t d, int schema, uint32_t W,
+                                                       uint32_t none) {
+    const uint32_t key = (uint32_t)d;
+    if (schema == GCC_SCHEMA_KV) return key;
+    switch ((uint32_t)(d >> 40) & 0xffu) {
+        case GCC_OE_W_READ: case GCC_OE_W_PAY: return key < W ? key : none;
+        case GCC_OE_D_NEWORDER: case GCC_OE_D_PAY: return key < 10u * W ? W + key : none;
+        case GCC_OE_C_READ: case GCC_OE_C_PAY: return key < 30000u * W ? 11u * W + key : none;
+        case GCC_OE_S_NEWORDER: return key < 100000u * W ? 30011u * W + key : none;
+        default: return none;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kernel arguments
+// ---------------------------------------------------------------------------
+struct ExecArgs {
+    // batch
+    const gcc_txn* txns;
+    const uint64_t* ops;          // gcc_op as packed 64-bit words
+    const ulonglong2* operands;
+    uint32_t n_txns;
+    uint64_t n_ops;
+    gcc_txn_result* results;
+    ulonglong2* reads;
+    // database
+    uint8_t* table;               // key-value slots (field-major)
+    uint64_t n_records;
+    uint32_t n_fields;
+    uint64_t* meta;               // one concurrency-control word per record
+    uint64_t n_meta;
+    int64_t* const* cols;         // order-entry columns (device array of pointers)
+    uint32_t n_warehouses;
+    uint32_t order_cap;
+    // scheme scratch
+    const uint32_t* need;         // DET: per-op wait threshold
+    unsigned long long* order_key;// OCC/TO: raw commit timestamp per txn
+    int order_key_uses_base;      // OCC: timestamps count from BatchState::ticket_base
+    BatchState* st;
+    DbState* dbs;
+    // policy
+    uint32_t lanes;               // lanes per transaction (power of two <= 32)
+    uint32_t max_ops;             // staging capacity per transaction
+    uint32_t collapse;
+    uint32_t backoff_base_ns;
+    uint32_t backoff_cap_ns;
+    uint32_t max_attempts;
+    uint32_t read_retries;
+    uint32_t inject_ppm;
+    uint64_t wait_budget_ns;
+    uint64_t deadline_ns;
+    uint64_t seed;
+};
+
+// Shared-memory staging per op: descriptor, observed word, value read and
+// value to write: the read and write sets live in shared memory while the
+// transaction runs, so aborted attempts never touch the output arrays.
+constexpr uint32_t STAGE_BYTES_PER_OP = 8 + 8 + 16 + 16;
+
+// ---------------------------------------------------------------------------
+// host-side launchers (one translation unit each)
+// ---------------------------------------------------------------------------
+// Key-value execute kernel for one scheme and slot width.
+cudaError_t launch_kv_exec(gcc_scheme scheme, uint32_t field_bytes, const ExecArgs& a,
+                           int grid, int block, size_t smem, cudaStream_t s);
+int kv_exec_occupancy(gcc_scheme scheme, uint32_t field_bytes, int block, size_t smem);
+// Order-entry execute kernel for one scheme.
+cudaError_t launch_oe_exec(gcc_scheme scheme, const ExecArgs& a, int grid, int block,
+                           size_t smem, cudaStream_t s);
+int oe_exec_occupancy(gcc_scheme scheme, int block, size_t smem);
+
+// Batch begin: zero the state; OCC: record the clock as ticket base.
+cudaError_t launch_batch_begin(BatchState* st, DbState* dbs, gcc_scheme scheme,
+                               cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) u32 pairs on the low `bits` bits.
+// Sorted output lands in (*keys_out, *vals_out), one of the two buffer pairs.
+struct SortScratch {
+    uint32_t *k0, *v0, *k1, *v1;
+    uint32_t* hist;               // 256 * max_tiles
+    uint32_t* totals;             // 256
+    size_t max_items;
+};
+size_t sort_max_tiles(size_t n);
+cudaError_t radix_sort_pairs(SortScratch& s, size_t n, int bits, uint32_t** keys_out,
+                             uint32_t** vals_out, cudaStream_t st);
+
+// Exclusive prefix sum of u32 (in place), with `tmp` of >= scan_tmp_words(n).
+size_t scan_tmp_words(size_t n);
+cudaError_t exclusive_scan_u32(uint32_t* data, size_t n, uint32_t* tmp, cudaStream_t st);
+
+// Deterministic-scheme preprocessing: access table (record, op) sorted by
+// record then transaction id, per-op wait thresholds and per-record counters.
+struct DetPrep {
+    const uint64_t* ops;
+    uint64_t n_ops;
+    uint64_t* meta;
+    uint32_t* need;
+    const uint32_t* op_cc_key;    // optional: concurrency-control record per op
+};
+cudaError_t det_prepare(const ExecArgs& a, SortScratch& s, uint32_t* scan_tmp, int key_bits,
+                        int schema, cudaStream_t st);
+
+// OCC / TO: replace raw commit timestamps by dense ranks 0..committed-1.
+cudaError_t densify_commit_order(const ExecArgs& a, SortScratch& s, cudaStream_t st);
+
+}  // namespace gcc

@@ -1,0 +1,339 @@
+"""Thin ctypes binding of the engine's C ABI (include/gcc_gb300.h).
+
+Argument marshalling only: every step of a batch runs in the CUDA library.
+The module-level ``gcc_*`` functions mirror the C entry points one to one;
+``Database`` and ``Batch`` wrap them for numpy inputs (host path) and torch
+CUDA tensors (device-resident path).  Loading fails loudly when the compiled
+library is absent -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import workload as wl
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgcc_gb300.so")
+
+SCHEMES = {"2pl": 0, "no_wait_2pl": 0, "to": 1, "occ": 2, "det": 3}
+SCHEME_NAMES = {0: "2pl", 1: "to", 2: "occ", 3: "det"}
+SCHEMA_KV, SCHEMA_ORDER_ENTRY = 0, 1
+TXN_PENDING, TXN_COMMITTED, TXN_TIMEOUT, TXN_INVALID = 0, 1, 2, 3
+STATUS = {0: "ok", 1: "invalid", 2: "cuda", 3: "timeout", 4: "nomem", 5: "device", 6: "capacity"}
+DEVERR = {0x1: "wait_budget", 0x2: "deadline", 0x4: "ts_overflow", 0x8: "attempts",
+          0x10: "invalid", 0x20: "insert"}
+WAIT_FOREVER = (1 << 64) - 1
+
+
+class DbDesc(ctypes.Structure):
+    _fields_ = [("schema", ctypes.c_uint32), ("field_bytes", ctypes.c_uint32),
+                ("n_records", ctypes.c_uint64), ("n_fields", ctypes.c_uint32),
+                ("n_warehouses", ctypes.c_uint32), ("order_cap", ctypes.c_uint32),
+                ("max_ops_per_txn", ctypes.c_uint32), ("max_batch_txns", ctypes.c_uint64),
+                ("max_batch_ops", ctypes.c_uint64), ("device", ctypes.c_int32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class ExecParams(ctypes.Structure):
+    _fields_ = [("lanes_per_txn", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
+                ("blocks_per_sm", ctypes.c_uint32), ("collapse", ctypes.c_uint32),
+                ("backoff_base_ns", ctypes.c_uint32), ("backoff_cap_ns", ctypes.c_uint32),
+                ("max_attempts", ctypes.c_uint32), ("read_retries", ctypes.c_uint32),
+                ("wait_budget_ns", ctypes.c_uint64), ("deadline_ns", ctypes.c_uint64),
+                ("seed", ctypes.c_uint64), ("inject_abort_ppm", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("n_txns", ctypes.c_uint64), ("committed", ctypes.c_uint64),
+                ("aborts", ctypes.c_uint64), ("timeouts", ctypes.c_uint64),
+                ("invalid", ctypes.c_uint64), ("max_attempts", ctypes.c_uint64),
+                ("device_error", ctypes.c_uint32), ("scheme", ctypes.c_uint32),
+                ("elapsed_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["scheme"] = SCHEME_NAMES.get(d["scheme"], d["scheme"])
+        d["abort_rate"] = d["aborts"] / d["committed"] if d["committed"] else float("nan")
+        d["errors"] = [n for b, n in DEVERR.items() if d["device_error"] & b]
+        return d
+
+
+class GCCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+P = ctypes.c_void_p
+
+# name -> (restype, argtypes); mirrors include/gcc_gb300.h
+SIGNATURES = {
+    "gcc_db_create": (ctypes.c_int, [ctypes.POINTER(DbDesc), ctypes.POINTER(P)]),
+    "gcc_db_destroy": (ctypes.c_int, [P]),
+    "gcc_table_count": (ctypes.c_uint32, [P]),
+    "gcc_table_bytes": (ctypes.c_uint64, [P, ctypes.c_uint32]),
+    "gcc_load_table": (ctypes.c_int, [P, ctypes.c_uint32, P, ctypes.c_uint64, ctypes.c_int]),
+    "gcc_db_read_table": (ctypes.c_int, [P, ctypes.c_uint32, P, ctypes.c_uint64, ctypes.c_int]),
+    "gcc_default_params": (ctypes.c_int, [ctypes.POINTER(ExecParams)]),
+    "gcc_txn_batch_submit": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_uint32, P, P,
+                                            ctypes.c_uint64, ctypes.c_int,
+                                            ctypes.POINTER(ExecParams), P, ctypes.POINTER(P)]),
+    "gcc_batch_wait": (ctypes.c_int, [P, ctypes.c_uint64, P, P, ctypes.POINTER(BatchStats),
+                                      ctypes.c_int]),
+    "gcc_batch_free": (ctypes.c_int, [P]),
+    "gcc_execute": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_uint32, P, P, ctypes.c_uint64,
+                                   ctypes.POINTER(ExecParams), P, P, P]),
+    "gcc_last_stats": (ctypes.c_int, [P, ctypes.POINTER(BatchStats)]),
+    "gcc_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load the compiled engine; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA engine library not found at {path}; build it first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise GCCError(status, load().gcc_last_error().decode(errors="replace"))
+
+
+def params(**kw) -> ExecParams:
+    """Execution parameters: the library defaults overridden by ``kw``."""
+    p = ExecParams()
+    _check(load().gcc_default_params(ctypes.byref(p)))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, int(v))
+    return p
+
+
+def _scheme(s) -> int:
+    return SCHEMES[s.lower()] if isinstance(s, str) else int(s)
+
+
+def _host_ptr(a: np.ndarray) -> int:
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data
+
+
+def _tensor_ptr(t) -> int:
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers
+# ---------------------------------------------------------------------------
+def gcc_db_create(desc: DbDesc) -> int:
+    h = P()
+    _check(load().gcc_db_create(ctypes.byref(desc), ctypes.byref(h)))
+    return h.value
+
+
+def gcc_db_destroy(db: int):
+    _check(load().gcc_db_destroy(db))
+
+
+def gcc_load_table(db: int, table_id: int, src_ptr: int, nbytes: int, on_device: bool):
+    _check(load().gcc_load_table(db, table_id, src_ptr, nbytes, int(on_device)))
+
+
+def gcc_db_read_table(db: int, table_id: int, dst_ptr: int, nbytes: int, on_device: bool):
+    _check(load().gcc_db_read_table(db, table_id, dst_ptr, nbytes, int(on_device)))
+
+
+def gcc_txn_batch_submit(db: int, scheme, txns_ptr: int, n_txns: int, ops_ptr: int,
+                         operands_ptr: int, n_ops: int, inputs_on_device: bool,
+                         p: Optional[ExecParams] = None, stream: int = 0) -> int:
+    h = P()
+    _check(load().gcc_txn_batch_submit(db, _scheme(scheme), txns_ptr, n_txns, ops_ptr,
+                                       operands_ptr, n_ops, int(inputs_on_device),
+                                       ctypes.byref(p) if p is not None else None,
+                                       stream or None, ctypes.byref(h)))
+    return h.value
+
+
+def gcc_batch_wait(batch: int, timeout_ns: int, results_ptr, reads_ptr,
+                   outputs_on_device: bool = False, check: bool = True) -> dict:
+    st = BatchStats()
+    rc = load().gcc_batch_wait(batch, timeout_ns, results_ptr, reads_ptr, ctypes.byref(st),
+                               int(outputs_on_device))
+    if check and rc not in (0, 5):
+        _check(rc)
+    d = st.as_dict()
+    d["status"] = STATUS.get(rc, rc)
+    return d
+
+
+def gcc_batch_free(batch: int):
+    _check(load().gcc_batch_free(batch))
+
+
+def gcc_execute(db: int, scheme, txns_ptr: int, n_txns: int, ops_ptr: int, operands_ptr: int,
+                n_ops: int, p: Optional[ExecParams], results_ptr: int, reads_ptr: int,
+                stream: int = 0):
+    _check(load().gcc_execute(db, _scheme(scheme), txns_ptr, n_txns, ops_ptr, operands_ptr,
+                              n_ops, ctypes.byref(p) if p is not None else None, results_ptr,
+                              reads_ptr, stream or None))
+
+
+def gcc_last_stats(db: int) -> dict:
+    st = BatchStats()
+    _check(load().gcc_last_stats(db, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def gcc_last_error() -> str:
+    return load().gcc_last_error().decode(errors="replace")
+
+
+# ---------------------------------------------------------------------------
+# object wrappers
+# ---------------------------------------------------------------------------
+class Database:
+    """A device-resident database: key-value (one field-major table) or
+    order-entry (22 int64 column tables)."""
+
+    def __init__(self, schema: str = "kv", *, n_records: int = 0, n_fields: int = 0,
+                 field_bytes: int = 8, n_warehouses: int = 0, order_cap: int = 0,
+                 max_ops_per_txn: int = 16, max_batch_txns: int = 1 << 16,
+                 max_batch_ops: Optional[int] = None, device: int = 0):
+        d = DbDesc()
+        d.schema = SCHEMA_KV if schema == "kv" else SCHEMA_ORDER_ENTRY
+        d.field_bytes = field_bytes
+        d.n_records = n_records
+        d.n_fields = n_fields
+        d.n_warehouses = n_warehouses
+        d.order_cap = order_cap
+        d.max_ops_per_txn = max_ops_per_txn
+        d.max_batch_txns = max_batch_txns
+        d.max_batch_ops = max_batch_ops or max_batch_txns * max_ops_per_txn
+        d.device = device
+        self.desc = d
+        self.schema = schema
+        self.handle = gcc_db_create(d)
+
+    def close(self):
+        if self.handle:
+            gcc_db_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def table_bytes(self, table_id: int = 0) -> int:
+        return int(load().gcc_table_bytes(self.handle, table_id))
+
+    def load_table(self, table_id: int, src):
+        """Copy a numpy array or a CUDA tensor into a table (resets control words)."""
+        if isinstance(src, np.ndarray):
+            src = np.ascontiguousarray(src)
+            gcc_load_table(self.handle, table_id, _host_ptr(src), src.nbytes, False)
+        else:
+            gcc_load_table(self.handle, table_id, _tensor_ptr(src),
+                           src.numel() * src.element_size(), True)
+
+    def read_table(self, table_id: int = 0, dtype=np.uint64) -> np.ndarray:
+        nbytes = self.table_bytes(table_id)
+        out = np.empty(nbytes // np.dtype(dtype).itemsize, dtype=dtype)
+        gcc_db_read_table(self.handle, table_id, _host_ptr(out), nbytes, False)
+        return out
+
+    # key-value helpers -----------------------------------------------------
+    def load_kv(self, table: np.ndarray):
+        self.load_table(0, table)
+
+    def read_kv(self) -> np.ndarray:
+        d = self.desc
+        t = self.read_table(0)
+        return t.reshape(d.n_fields, d.n_records) if d.field_bytes == 8 else \
+            t.reshape(d.n_fields, d.n_records, 2)
+
+    # order-entry helpers ---------------------------------------------------
+    def load_oe(self, db: dict):
+        for i, c in enumerate(wl.OE_COLUMNS):
+            self.load_table(i, np.ascontiguousarray(db[c], dtype=np.int64))
+
+    def read_oe(self) -> dict:
+        return {c: self.read_table(i, dtype=np.int64) for i, c in enumerate(wl.OE_COLUMNS)}
+
+    # execution -------------------------------------------------------------
+    def submit(self, scheme, batch: "wl.KVBatch", p: Optional[ExecParams] = None,
+               stream: int = 0) -> "Batch":
+        """Host-input submission: inputs are copied before this returns."""
+        txns = np.ascontiguousarray(batch.txns)
+        ops = np.ascontiguousarray(batch.ops)
+        operands = np.ascontiguousarray(batch.operands, dtype=np.uint64)
+        h = gcc_txn_batch_submit(self.handle, scheme, _host_ptr(txns), batch.n_txns,
+                                 _host_ptr(ops), _host_ptr(operands), batch.n_ops, False, p,
+                                 stream)
+        return Batch(h, batch.n_txns, batch.n_ops)
+
+    def run(self, scheme, batch, p: Optional[ExecParams] = None, timeout_s: float = 120.0):
+        """Submit, wait, and return (results, reads uint64[n_ops, 2], stats)."""
+        b = self.submit(scheme, batch, p)
+        try:
+            return b.wait(timeout_s)
+        finally:
+            b.free()
+
+    def execute(self, scheme, d_txns, d_ops, d_operands, n_txns: int, n_ops: int, d_results,
+                d_reads, p: Optional[ExecParams] = None, stream: int = 0):
+        """Device-resident execution on torch CUDA tensors (asynchronous)."""
+        gcc_execute(self.handle, scheme, _tensor_ptr(d_txns), n_txns, _tensor_ptr(d_ops),
+                    _tensor_ptr(d_operands), n_ops, p, _tensor_ptr(d_results),
+                    _tensor_ptr(d_reads), stream)
+
+    def last_stats(self) -> dict:
+        return gcc_last_stats(self.handle)
+
+
+class Batch:
+    def __init__(self, handle: int, n_txns: int, n_ops: int):
+        self.handle, self.n_txns, self.n_ops = handle, n_txns, n_ops
+
+    def wait(self, timeout_s: Optional[float] = None, results: Optional[np.ndarray] = None,
+             reads: Optional[np.ndarray] = None):
+        results = np.zeros(self.n_txns, dtype=wl.RESULT_DTYPE) if results is None else results
+        reads = np.zeros((self.n_ops, 2), dtype=np.uint64) if reads is None else reads
+        t = WAIT_FOREVER if timeout_s is None else int(timeout_s * 1e9)
+        stats = gcc_batch_wait(self.handle, t, _host_ptr(results) if self.n_txns else None,
+                               _host_ptr(reads) if self.n_ops else None)
+        return results, reads, stats
+
+    def free(self):
+        if self.handle:
+            gcc_batch_free(self.handle)
+            self.handle = 0
