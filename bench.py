@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark: committed transactions/s and abort rate of one GPU batch.
+
+A step is one batch of 2^20 key-value transactions (16 ops each over 2^24
+records x 10 fields in 16-byte slots, Zipfian keys) through the whole
+execution path: control-word setup, [deterministic preprocessing], the
+execute kernel and the dense commit ranks.  Inputs are resident in HBM when
+the timed region starts; the table (2.5 GiB) and the batch (400 MB) are
+larger than L2, so no flush is needed between steps.
+
+The headline line is OCC at theta 0.8, read ratio 0.5; ``schemes`` adds the
+same workload under every scheme.  ``--impl reference`` times the CPU oracle
+(single-threaded serial execution) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "committed txns/s + abort rate on 1 GB300 vs plain launch; p99 commit latency"
+SCHEMES = ["occ", "2pl", "to", "det"]
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--scheme", default="occ", choices=SCHEMES)
+    p.add_argument("--theta", type=float, default=0.8)
+    p.add_argument("--read-ratio", type=float, default=0.5)
+    p.add_argument("--records", type=int, default=1 << 24)
+    p.add_argument("--txns", type=int, default=1 << 20)
+    p.add_argument("--lanes", type=int, default=0, help="lanes per transaction (0 = default)")
+    p.add_argument("--warps", type=int, default=0, help="warps per block (0 = default)")
+    p.add_argument("--no-schemes", action="store_true", help="skip the per-scheme lines")
+    p.add_argument("--scheme-steps", type=int, default=5)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--seed", type=int, default=0x5EED0002)
+    return p.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the GPU works."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for _, _, p in rows for n, v in zip(names, p[5:9]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def algorithmic_bytes(batch) -> dict:
+    """Bytes the method must move per batch (useful bytes): per transaction
+    its 8-byte descriptor and 16-byte result; per READ op 8 descriptor + 8
+    control word + 16 slot + 8 control-word revalidation + 16 value out; per
+    read-modify-write op 8 descriptor + 16 operand + 16 slot read + 16 slot
+    write + 8 lock + 8 unlock/version + 16 value out."""
+    from paper_2406_10158_gb300 import workload as wl
+    n_w = int(np.count_nonzero(batch.ops["kind"] == wl.OP_ADD))
+    n_r = batch.n_ops - n_w
+    per_txn = 8 + 16
+    total = batch.n_txns * per_txn + n_r * 56 + n_w * 88
+    return {"bytes": total, "reads": n_r, "writes": n_w, "per_txn": total / max(1, batch.n_txns)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def time_oracle(table, batch, seconds: float, max_txns=None):
+    """Single-threaded serial execution (the CPU oracle) of a prefix of the
+    batch, repeated until about ``seconds`` have passed; returns txn/s."""
+    import oracle
+    from paper_2406_10158_gb300 import workload as wl
+    n = batch.n_txns if max_txns is None else min(batch.n_txns, max_txns)
+    sub = wl.KVBatch(txns=batch.txns[:n], ops=batch.ops, operands=batch.operands)
+    work = table.copy()
+    done, t_total, reps = 0, 0.0, 0
+    while t_total < seconds or reps == 0:
+        t0 = time.perf_counter()
+        oracle.serial_inplace(work, sub)
+        t_total += time.perf_counter() - t0
+        done += n
+        reps += 1
+        if reps >= 50:
+            break
+    return done / t_total, {"txns": n, "repeats": reps, "seconds": round(t_total, 3)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_2406_10158_gb300 import workload as wl
+    table, batch = wl.ycsb_kv(args.seed, theta=args.theta, read_ratio=args.read_ratio,
+                              nrec=args.records, n_txns=args.txns)
+    sample = min(batch.n_txns, 1 << 17)
+    import oracle
+    sub = wl.KVBatch(txns=batch.txns[:sample], ops=batch.ops, operands=batch.operands)
+    work = table.copy()
+    for _ in range(max(0, args.warmup)):
+        oracle.serial_inplace(work, sub)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.serial_inplace(work, sub)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = sample * args.steps / total
+    workload = config_dict(args)
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "txn/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": workload,
+            "cpu_baseline": {"value": value, "unit": "txn/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {sample} of {batch.n_txns} txns per step, "
+                                       "serial in transaction-id order"},
+            "e2e": {"value": value, "unit": "txn/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def config_dict(args):
+    return {"workload": f"kv 16B slots {args.records}x10, {args.txns} txns x 16 ops, "
+                        f"zipf {args.theta}, read ratio {args.read_ratio}",
+            "scheme": args.scheme, "records": args.records, "fields": 10, "slot_bytes": 16,
+            "txns_per_batch": args.txns, "ops_per_txn": 16, "theta": args.theta,
+            "read_ratio": args.read_ratio,
+            "l2": "inputs larger than L2 (2.5 GiB table, 400 MB batch); no flush",
+            "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, dist):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_10158_gb300 import engine as eng
+    from paper_2406_10158_gb300 import workload as wl
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    table, batch = wl.ycsb_kv(args.seed + rank, theta=args.theta, read_ratio=args.read_ratio,
+                              nrec=args.records, n_txns=args.txns)
+    db = eng.Database("kv", n_records=args.records, n_fields=10, field_bytes=16,
+                      max_ops_per_txn=16, max_batch_txns=args.txns, device=dev)
+    db.load_kv(table)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    t_txns = torch.from_numpy(batch.txns.view(np.uint8)).to(dev)
+    t_ops = torch.from_numpy(batch.ops.view(np.uint8)).to(dev)
+    t_operands = torch.from_numpy(batch.operands.view(np.uint8).reshape(-1)).to(dev)
+    t_res = torch.empty(batch.n_txns * 16, dtype=torch.uint8, device=dev)
+    t_reads = torch.empty(batch.n_ops * 16, dtype=torch.uint8, device=dev)
+    kw = {}
+    if args.lanes:
+        kw["lanes_per_txn"] = args.lanes
+    if args.warps:
+        kw["warps_per_block"] = args.warps
+    prm = eng.params(**kw)
+
+    def step(scheme):
+        db.execute(scheme, t_txns, t_ops, t_operands, batch.n_txns, batch.n_ops, t_res, t_reads,
+                   prm, sh)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    def timed(scheme, steps, warmup):
+        for _ in range(warmup):
+            step(scheme)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step(scheme)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        hist = db.stage_history(steps)
+        stats = db.last_stats()
+        return ms, hist, stats
+
+    with ClockSampler(dev) as clocks:
+        ms, hist, stats = timed(args.scheme, args.steps, args.warmup)
+        ms_max = ms
+        if dist is not None:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_max = float(t.item())
+        committed = stats["committed"]
+        value = committed * args.steps * world / (ms_max / 1000.0)
+        kernel_ms = statistics.mean(h["kernel_ms"] for h in hist)
+        launches = sum(h["kernel_launches"] for h in hist)
+
+        # per-scheme lines on the same workload
+        schemes = {}
+        if not args.no_schemes:
+            for s in SCHEMES:
+                sms, shist, sst = timed(s, args.scheme_steps, 1)
+                schemes[s] = {
+                    "committed_txn_per_s": sst["committed"] * args.scheme_steps / (sms / 1000.0),
+                    "abort_rate": sst["abort_rate"], "ms_per_batch": sms / args.scheme_steps,
+                    "prep_ms": statistics.mean(h["prep_ms"] for h in shist),
+                    "kernel_ms": statistics.mean(h["kernel_ms"] for h in shist),
+                    "order_ms": statistics.mean(h["order_ms"] for h in shist),
+                    "all_committed": sst["committed"] == batch.n_txns,
+                }
+
+        # end to end through the public API with host buffers
+        e2e = None
+        if not args.no_e2e:
+            pin = lambda a: torch.from_numpy(a.view(np.uint8).reshape(-1)).pin_memory()
+            h_txns, h_ops, h_opd = pin(batch.txns), pin(batch.ops), pin(batch.operands)
+            h_res = torch.empty(batch.n_txns * 16, dtype=torch.uint8).pin_memory()
+            h_reads = torch.empty(batch.n_ops * 16, dtype=torch.uint8).pin_memory()
+            e2e_steps = max(3, min(args.steps, 10))
+
+            def api_step():
+                b = eng.gcc_txn_batch_submit(db.handle, args.scheme, h_txns.data_ptr(),
+                                             batch.n_txns, h_ops.data_ptr(), h_opd.data_ptr(),
+                                             batch.n_ops, False, prm, sh)
+                st = eng.gcc_batch_wait(b, eng.WAIT_FOREVER, h_res.data_ptr(), h_reads.data_ptr())
+                eng.gcc_batch_free(b)
+                return st
+
+            api_step()
+            barrier()
+            t0 = time.perf_counter()
+            committed_e2e = 0
+            for _ in range(e2e_steps):
+                committed_e2e += api_step()["committed"]
+            barrier()
+            dt = time.perf_counter() - t0
+            if dist is not None:
+                t = torch.tensor([dt], dtype=torch.float64, device=dev)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                dt = float(t.item())
+            e2e = {"value": committed_e2e * world / dt, "unit": "txn/s",
+                   "h2d_bytes_per_step": batch.n_txns * 8 + batch.n_ops * 24,
+                   "d2h_bytes_per_step": batch.n_txns * 16 + batch.n_ops * 16,
+                   "steps": e2e_steps, "api": "gcc_txn_batch_submit + gcc_batch_wait"}
+    clock = clocks.summary()
+
+    if rank != 0:
+        db.close()
+        return None
+
+    alg = algorithmic_bytes(batch)
+    peak, peak_kind = measured_peaks()
+    achieved = alg["bytes"] / (kernel_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": f"kv_exec_kernel<{args.scheme}>", "kernel_ms": round(kernel_ms, 4),
+                "algorithmic_bytes_per_launch": alg["bytes"],
+                "algorithmic_bytes_per_txn": round(alg["per_txn"], 1),
+                "peak_kind": f"{peak_kind} hbm_gbs"}
+    cpu = None
+    if not args.no_cpu:
+        v, info = time_oracle(table, batch, args.cpu_seconds, max_txns=1 << 18)
+        cpu = {"value": v, "unit": "txn/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {info['txns']} txns of the batch, serial in id order, "
+                         f"{info['repeats']} repeats, {info['seconds']} s"}
+    out = {"metric": METRIC, "value": value, "unit": "txn/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+           "data": "synthetic", "config": config_dict(args),
+           "abort_rate": stats["abort_rate"], "all_committed": committed == batch.n_txns,
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock,
+           "gpu_launches": launches, "schemes": schemes}
+    db.close()
+    return out
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference" and rank != 0:
+        return                       # the CPU oracle runs on rank 0 only
+    if world > 1 and args.impl == "ours":
+        # replicas: the process group only carries the timing barrier and max
+        import torch
+        import torch.distributed as dist_mod
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, dist)
+    if out is not None and rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -155,8 +155,9 @@ typedef struct gcc_exec_params {
     uint32_t collapse;         /* 1 = collapse same-key lock attempts inside a
                                   warp before they reach global atomics [1];
                                   2 = off */
-    uint32_t backoff_base_ns;  /* first retry delay, doubled per abort [0 = none] */
-    uint32_t backoff_cap_ns;   /* largest retry delay [100000] */
+    uint32_t backoff_base_ns;  /* first retry delay, doubled per abort, with
+                                  random jitter [128] */
+    uint32_t backoff_cap_ns;   /* largest retry delay [65536] */
     uint32_t max_attempts;     /* per transaction, then GCC_TXN_TIMEOUT [2^24] */
     uint32_t read_retries;     /* re-reads of a record seen mid-update before
                                   the attempt aborts [8] */
@@ -166,7 +167,8 @@ typedef struct gcc_exec_params {
     uint64_t seed;             /* retry jitter and abort injection */
     uint32_t inject_abort_ppm; /* test hook: abort an attempt at its commit point
                                   with this probability per million [0] */
-    uint32_t reserved;         /* 0 */
+    uint32_t immediate_restart;/* 1 = restart an aborted transaction at once, with
+                                  no delay (the paper's policy) [0] */
 } gcc_exec_params;
 
 typedef struct gcc_batch_stats {
@@ -179,7 +181,25 @@ typedef struct gcc_batch_stats {
     uint32_t device_error;     /* GCC_DEVERR_* bits */
     uint32_t scheme;
     double elapsed_ms;         /* device time of the batch (submit/wait only) */
+    double prep_ms;            /* stage times from CUDA events on the batch's
+                                  stream: control-word reset, batch begin and
+                                  deterministic preprocessing */
+    double kernel_ms;          /* the execute kernel */
+    double order_ms;           /* dense commit ranks */
+    uint32_t kernel_launches;  /* kernels this execution launched */
+    uint32_t grid_blocks;      /* blocks of the execute kernel */
 } gcc_batch_stats;
+
+/* Stage times of one past execution (see gcc_stage_history). */
+typedef struct gcc_stage_times {
+    double prep_ms;
+    double kernel_ms;
+    double order_ms;
+    uint32_t scheme;
+    uint32_t n_txns;
+    uint32_t kernel_launches;
+    uint32_t grid_blocks;
+} gcc_stage_times;
 
 /* device_error bits */
 #define GCC_DEVERR_WAIT_BUDGET   0x1u   /* a deterministic wait ran out        */
@@ -266,6 +286,12 @@ gcc_status gcc_execute(gcc_db *db, gcc_scheme scheme, const gcc_txn *d_txns,
 /* Statistics of the latest gcc_execute / submit on db (synchronises its
  * stream; elapsed_ms is 0 for gcc_execute). */
 gcc_status gcc_last_stats(gcc_db *db, gcc_batch_stats *stats);
+
+/* Stage times of the latest executions on db, oldest first: up to max_entries
+ * of the last 256, written to out; *n_out receives the count.  Synchronises
+ * the streams they ran on. */
+gcc_status gcc_stage_history(gcc_db *db, uint32_t max_entries, gcc_stage_times *out,
+                             uint32_t *n_out);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *gcc_last_error(void);

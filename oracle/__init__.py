@@ -147,6 +147,17 @@ def serial(table: np.ndarray, batch, order=None, lib=None):
     return work, reads
 
 
+def serial_inplace(table: np.ndarray, batch, order=None, lib=None):
+    """Serial execution directly on ``table`` without recording reads (the
+    benchmark's CPU baseline times this call)."""
+    lib = lib or load()
+    kv = _kv(table, _field_bytes(table))
+    o = None if order is None else np.ascontiguousarray(order, dtype=np.uint32)
+    e = lib.orc_kv_serial(ctypes.byref(kv), _p(batch.txns), batch.n_txns, _p(batch.ops),
+                          _p(batch.operands), _p(o), 0 if o is None else o.size, None)
+    _check(e, "serial execution")
+
+
 def commit_sequence(results: np.ndarray, lib=None) -> np.ndarray:
     """Committed transaction ids in reported commit order (checks permutation)."""
     lib = lib or load()

@@ -57,6 +57,15 @@ uint64_t oe_rows(uint32_t col, uint64_t W, uint64_t cap) {
 
 enum MetaState { META_ZERO, META_OCC, META_TO, META_DET, META_UNKNOWN };
 
+// CUDA events bracketing the stages of one execution.
+struct StageRec {
+    cudaEvent_t ev[4] = {};        // start, before execute kernel, after it, end
+    cudaStream_t stream = nullptr;
+    uint32_t scheme = 0, n_txns = 0, launches = 0, grid = 0;
+    bool used = false;
+};
+constexpr uint32_t STAGE_RING = 256;
+
 }  // namespace
 
 struct gcc_db {
@@ -88,6 +97,9 @@ struct gcc_db {
     // pinned copies of BatchState for submitted batches
     gcc::BatchState* h_states = nullptr;
     uint32_t n_h_states = 0, next_h_state = 0;
+    // stage timing ring
+    StageRec stages[STAGE_RING];
+    uint64_t n_stages = 0;
 };
 
 struct gcc_batch {
@@ -101,6 +113,7 @@ struct gcc_batch {
     gcc_operand* d_reads = nullptr;
     gcc::BatchState* h_state = nullptr;   // pinned, filled at batch end
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+    uint64_t stage_index = 0;             // its entry in the database's stage ring
 };
 
 namespace {
@@ -111,8 +124,8 @@ gcc_exec_params defaults() {
     p.warps_per_block = 8;
     p.blocks_per_sm = 0;
     p.collapse = 1;
-    p.backoff_base_ns = 0;
-    p.backoff_cap_ns = 100000;
+    p.backoff_base_ns = 128;
+    p.backoff_cap_ns = 65536;
     p.max_attempts = 1u << 24;
     p.read_retries = 8;
     p.wait_budget_ns = 2000000000ull;
@@ -129,8 +142,9 @@ gcc_exec_params merged(const gcc_exec_params* in) {
     if (in->warps_per_block) p.warps_per_block = in->warps_per_block;
     p.blocks_per_sm = in->blocks_per_sm;
     if (in->collapse) p.collapse = in->collapse;
-    p.backoff_base_ns = in->backoff_base_ns;
+    if (in->backoff_base_ns) p.backoff_base_ns = in->backoff_base_ns;
     if (in->backoff_cap_ns) p.backoff_cap_ns = in->backoff_cap_ns;
+    p.immediate_restart = in->immediate_restart;
     if (in->max_attempts) p.max_attempts = in->max_attempts;
     if (in->read_retries) p.read_retries = in->read_retries;
     if (in->wait_budget_ns) p.wait_budget_ns = in->wait_budget_ns;
@@ -180,6 +194,9 @@ void free_db(gcc_db* db) {
     cudaFree(db->need);
     cudaFree(db->order_key);
     if (db->h_states) cudaFreeHost(db->h_states);
+    for (auto& r : db->stages)
+        for (auto& e : r.ev)
+            if (e) cudaEventDestroy(e);
     if (db->stream) cudaStreamDestroy(db->stream);
     delete db;
 }
@@ -258,6 +275,10 @@ gcc_status create_impl(const gcc_db_desc* desc, gcc_db** out) {
     db->n_h_states = 256;
     if (cudaMallocHost(&db->h_states, sizeof(gcc::BatchState) * db->n_h_states) != cudaSuccess)
         return bail(fail(GCC_ERR_NOMEM, "cannot allocate pinned batch states"));
+    for (auto& r : db->stages)
+        for (auto& e : r.ev)
+            if (cudaEventCreate(&e) != cudaSuccess)
+                return bail(fail(GCC_ERR_CUDA, "cannot create timing events"));
     *out = db;
     return GCC_OK;
 }
@@ -288,6 +309,9 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     if (s) return s;
     GCC_CK(cudaSetDevice(db->d.device));
     cudaStream_t st = stream ? stream : db->stream;
+    StageRec& rec = db->stages[db->n_stages % STAGE_RING];
+    GCC_CK(cudaEventRecord(rec.ev[0], st));
+    uint32_t launches = 0;
 
     // control words: reset whenever the previous batch left them in a state
     // the scheme cannot start from
@@ -324,7 +348,7 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     a.lanes = p.lanes_per_txn;
     a.max_ops = db->d.max_ops_per_txn;
     a.collapse = p.collapse;
-    a.backoff_base_ns = p.backoff_base_ns;
+    a.backoff_base_ns = p.immediate_restart ? 0u : p.backoff_base_ns;
     a.backoff_cap_ns = p.backoff_cap_ns;
     a.max_attempts = p.max_attempts;
     a.read_retries = p.read_retries;
@@ -334,10 +358,12 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     a.seed = p.seed;
 
     GCC_CK(gcc::launch_batch_begin(db->st, db->dbs, scheme, st));
+    launches += 1;
     const bool kv = db->d.schema == GCC_SCHEMA_KV;
-    if (scheme == GCC_DET) {
-        const int bits = kv ? bit_length(db->n_meta - 1) : bit_length(db->n_meta);
-        GCC_CK(gcc::det_prepare(a, db->sort, db->scan_tmp, std::max(bits, 1), db->d.schema, st));
+    if (scheme == GCC_DET && n_ops) {
+        const int bits = std::max(1, kv ? bit_length(db->n_meta - 1) : bit_length(db->n_meta));
+        GCC_CK(gcc::det_prepare(a, db->sort, db->scan_tmp, bits, db->d.schema, st));
+        launches += 1 + 3 * ((bits + 7) / 8) + 1 + 3 + 1;   // emit, sort, flags, scan, need
     }
     const int block = (int)p.warps_per_block * 32;
     const uint32_t slots = block / p.lanes_per_txn;
@@ -351,12 +377,25 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     int64_t grid = (int64_t)db->sm_count * per_sm;
     const int64_t needed = ((int64_t)n_txns + slots - 1) / slots;
     grid = std::max<int64_t>(1, std::min(grid, needed));
+    GCC_CK(cudaEventRecord(rec.ev[1], st));
     if (n_txns) {
         GCC_CK(kv ? gcc::launch_kv_exec(scheme, db->d.field_bytes, a, (int)grid, block, smem, st)
                   : gcc::launch_oe_exec(scheme, a, (int)grid, block, smem, st));
-        if (scheme == GCC_OCC || scheme == GCC_TO)
-            GCC_CK(gcc::densify_commit_order(a, db->sort, st));
+        launches += 1;
     }
+    GCC_CK(cudaEventRecord(rec.ev[2], st));
+    if (n_txns && (scheme == GCC_OCC || scheme == GCC_TO)) {
+        GCC_CK(gcc::densify_commit_order(a, db->sort, st));
+        launches += 1 + 3 * 4 + 1;                           // emit, 4 sort passes, rank
+    }
+    GCC_CK(cudaEventRecord(rec.ev[3], st));
+    rec.stream = st;
+    rec.scheme = scheme;
+    rec.n_txns = n_txns;
+    rec.launches = launches;
+    rec.grid = n_txns ? (uint32_t)grid : 0u;
+    rec.used = true;
+    db->n_stages++;
     switch (scheme) {
         case GCC_NO_WAIT_2PL: db->meta_state = META_ZERO; break;
         case GCC_OCC: db->meta_state = META_OCC; break;
@@ -369,7 +408,23 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     return GCC_OK;
 }
 
-void fill_stats(const gcc::BatchState& h, gcc_scheme scheme, uint64_t n_txns, gcc_batch_stats* s) {
+// Stage times of a completed execution (its events must have been reached).
+gcc_stage_times stage_times(const StageRec& r) {
+    gcc_stage_times t{};
+    float a = 0.f, b = 0.f, c = 0.f;
+    if (cudaEventElapsedTime(&a, r.ev[0], r.ev[1]) == cudaSuccess) t.prep_ms = a;
+    if (cudaEventElapsedTime(&b, r.ev[1], r.ev[2]) == cudaSuccess) t.kernel_ms = b;
+    if (cudaEventElapsedTime(&c, r.ev[2], r.ev[3]) == cudaSuccess) t.order_ms = c;
+    t.scheme = r.scheme;
+    t.n_txns = r.n_txns;
+    t.kernel_launches = r.launches;
+    t.grid_blocks = r.grid;
+    return t;
+}
+
+void fill_stats(const gcc::BatchState& h, gcc_scheme scheme, uint64_t n_txns,
+                const StageRec* r, gcc_batch_stats* s) {
+    *s = gcc_batch_stats{};
     s->n_txns = n_txns;
     s->committed = h.committed;
     s->aborts = h.aborts;
@@ -378,7 +433,14 @@ void fill_stats(const gcc::BatchState& h, gcc_scheme scheme, uint64_t n_txns, gc
     s->max_attempts = h.max_attempts;
     s->device_error = h.error;
     s->scheme = scheme;
-    s->elapsed_ms = 0.0;
+    if (r && r->used) {
+        const gcc_stage_times t = stage_times(*r);
+        s->prep_ms = t.prep_ms;
+        s->kernel_ms = t.kernel_ms;
+        s->order_ms = t.order_ms;
+        s->kernel_launches = t.kernel_launches;
+        s->grid_blocks = t.grid_blocks;
+    }
 }
 
 }  // namespace
@@ -462,7 +524,23 @@ gcc_status gcc_last_stats(gcc_db* db, gcc_batch_stats* stats) {
     gcc::BatchState h{};
     GCC_CK(cudaStreamSynchronize(db->last_stream ? db->last_stream : db->stream));
     GCC_CK(cudaMemcpy(&h, db->st, sizeof h, cudaMemcpyDeviceToHost));
-    fill_stats(h, db->last_scheme, db->last_n_txns, stats);
+    const StageRec* r = db->n_stages ? &db->stages[(db->n_stages - 1) % STAGE_RING] : nullptr;
+    fill_stats(h, db->last_scheme, db->last_n_txns, r, stats);
+    return GCC_OK;
+}
+
+gcc_status gcc_stage_history(gcc_db* db, uint32_t max_entries, gcc_stage_times* out,
+                             uint32_t* n_out) {
+    if (!db || !n_out || (max_entries && !out)) return fail(GCC_ERR_INVALID, "null argument");
+    GCC_CK(cudaSetDevice(db->d.device));
+    const uint64_t avail = std::min<uint64_t>(db->n_stages, STAGE_RING);
+    const uint64_t n = std::min<uint64_t>(avail, max_entries);
+    for (uint64_t i = 0; i < n; ++i) {
+        const StageRec& r = db->stages[(db->n_stages - n + i) % STAGE_RING];
+        GCC_CK(cudaEventSynchronize(r.ev[3]));
+        out[i] = stage_times(r);
+    }
+    *n_out = (uint32_t)n;
     return GCC_OK;
 }
 
@@ -516,6 +594,7 @@ gcc_status gcc_txn_batch_submit(gcc_db* db, gcc_scheme scheme, const gcc_txn* tx
     if (n_ops && cudaMallocAsync(&b->d_reads, n_ops * sizeof(gcc_operand), b->stream))
         return bail(fail(GCC_ERR_NOMEM, "read-value buffer"));
     if (cudaEventRecord(b->ev_start, b->stream)) return bail(fail(GCC_ERR_CUDA, "event record"));
+    b->stage_index = db->n_stages;
     gcc_status s = execute_impl(db, scheme, d_txns, n_txns, d_ops, d_operands, n_ops, params,
                                 b->d_results, b->d_reads, b->stream);
     if (s) return bail(s);
@@ -552,7 +631,10 @@ gcc_status gcc_batch_wait(gcc_batch* b, uint64_t timeout_ns, gcc_txn_result* res
     GCC_CK(cudaStreamSynchronize(b->stream));
     gcc::BatchState h = *b->h_state;
     if (stats) {
-        fill_stats(h, b->scheme, b->n_txns, stats);
+        const gcc_db* db = b->db;
+        const bool live = db->n_stages - b->stage_index <= STAGE_RING;
+        fill_stats(h, b->scheme, b->n_txns,
+                   live ? &db->stages[b->stage_index % STAGE_RING] : nullptr, stats);
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, b->ev_start, b->ev_done) == cudaSuccess) stats->elapsed_ms = ms;
     }

@@ -45,7 +45,7 @@ class ExecParams(ctypes.Structure):
                 ("max_attempts", ctypes.c_uint32), ("read_retries", ctypes.c_uint32),
                 ("wait_budget_ns", ctypes.c_uint64), ("deadline_ns", ctypes.c_uint64),
                 ("seed", ctypes.c_uint64), ("inject_abort_ppm", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("immediate_restart", ctypes.c_uint32)]
 
 
 class BatchStats(ctypes.Structure):
@@ -53,7 +53,9 @@ class BatchStats(ctypes.Structure):
                 ("aborts", ctypes.c_uint64), ("timeouts", ctypes.c_uint64),
                 ("invalid", ctypes.c_uint64), ("max_attempts", ctypes.c_uint64),
                 ("device_error", ctypes.c_uint32), ("scheme", ctypes.c_uint32),
-                ("elapsed_ms", ctypes.c_double)]
+                ("elapsed_ms", ctypes.c_double), ("prep_ms", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double), ("order_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_uint32), ("grid_blocks", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -61,6 +63,16 @@ class BatchStats(ctypes.Structure):
         d["abort_rate"] = d["aborts"] / d["committed"] if d["committed"] else float("nan")
         d["errors"] = [n for b, n in DEVERR.items() if d["device_error"] & b]
         return d
+
+
+class StageTimes(ctypes.Structure):
+    _fields_ = [("prep_ms", ctypes.c_double), ("kernel_ms", ctypes.c_double),
+                ("order_ms", ctypes.c_double), ("scheme", ctypes.c_uint32),
+                ("n_txns", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint32),
+                ("grid_blocks", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class GCCError(RuntimeError):
@@ -90,6 +102,7 @@ SIGNATURES = {
     "gcc_execute": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_uint32, P, P, ctypes.c_uint64,
                                    ctypes.POINTER(ExecParams), P, P, P]),
     "gcc_last_stats": (ctypes.c_int, [P, ctypes.POINTER(BatchStats)]),
+    "gcc_stage_history": (ctypes.c_int, [P, ctypes.c_uint32, P, ctypes.POINTER(ctypes.c_uint32)]),
     "gcc_last_error": (ctypes.c_char_p, []),
 }
 
@@ -206,6 +219,13 @@ def gcc_last_stats(db: int) -> dict:
     return st.as_dict()
 
 
+def gcc_stage_history(db: int, max_entries: int = 256) -> list:
+    arr = (StageTimes * max(1, max_entries))()
+    n = ctypes.c_uint32(0)
+    _check(load().gcc_stage_history(db, max_entries, arr, ctypes.byref(n)))
+    return [arr[i].as_dict() for i in range(n.value)]
+
+
 def gcc_last_error() -> str:
     return load().gcc_last_error().decode(errors="replace")
 
@@ -318,6 +338,9 @@ class Database:
 
     def last_stats(self) -> dict:
         return gcc_last_stats(self.handle)
+
+    def stage_history(self, n: int = 256) -> list:
+        return gcc_stage_history(self.handle, n)
 
 
 class Batch:

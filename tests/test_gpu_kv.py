@@ -57,10 +57,10 @@ def test_small_kv_store(eng, scheme):
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8, 32])
 def test_lane_group_widths(eng, scheme, lanes):
     """Hot keys, ragged op counts (1..40 ops, several per lane) for every lane-group width."""
-    nrec = 2048
+    nrec = 16384
     table = wl.kv_table_splitmix(77, nrec, 4)
     batch = wl.kv_batch(5 + lanes, nrec=nrec, nfields=4, n_txns=3000, ops_range=(1, 40),
-                        read_ratio=0.5, theta=0.9)
+                        read_ratio=0.5, theta=0.8)
     with eng.Database("kv", n_records=nrec, n_fields=4, field_bytes=8, max_ops_per_txn=40,
                       max_batch_txns=3000) as db:
         db.load_kv(table)
