@@ -1,0 +1,577 @@
+// exec_common.cuh -- the execute kernel shared by every schema.
+//
+// A persistent kernel: a warp is split into lane groups of G lanes; each
+// group owns one transaction at a time, taken from a global counter in
+// transaction-id order (one atomic per warp).  Op j of a transaction is
+// handled by lane j mod G, so a group issues up to G independent record
+// accesses at once, and group-wide decisions (abort, commit) are ballots over
+// the group.  Per-op state -- descriptor, observed control word, value read,
+// value to write -- is staged in shared memory, so an aborted attempt never
+// touches the output arrays.
+//
+// The groups of a warp advance in rounds.  In a round every group that holds
+// a transaction and is not backing off makes one attempt; an aborted
+// transaction sits out a random number of rounds that grows with its abort
+// count, and a warp with no group attempting sleeps for one round quantum.
+// Locks, dirty bits and write locks are only ever held inside an attempt, so
+// a sleeping warp never holds any.  A transaction restarts until it commits
+// (Sec. IV-A, "Experimental Procedure"), within an attempt budget and a
+// kernel deadline.
+//
+// Schemes (Sec. II and Sec. III-E; control-word layouts in engine.cuh):
+//  * NO_WAIT 2PL  -- shared/exclusive lock per record taken before the access,
+//    abort as soon as a lock is unavailable, all locks released at commit or
+//    abort (Sec. II-A, Sec. III-E.1).  Writes are buffered and applied while
+//    the exclusive locks are held.  Commit order: a counter taken while every
+//    lock is held (the lock point).
+//  * TO           -- per-record RTS/WTS; a read needs ts > WTS, a write needs
+//    ts > RTS and ts > WTS, otherwise abort and restart with a new timestamp;
+//    a dirty bit locks uncommitted writes (Sec. II-B, Sec. III-E.2).  Commit
+//    order: the timestamp.
+//  * OCC          -- read phase into a private workspace with version checks,
+//    lock the write set without waiting (abort if locked), take a commit
+//    timestamp, validate the read set, write and release with the new version
+//    (Sec. II-B, Sec. III-E.2 Silo: lock bit + 63-bit timestamp, no epochs,
+//    no-wait locking).  Commit order: the timestamp.
+//  * DET          -- every op waits until the lower-id accesses to its record
+//    that conflict with it are done, then runs; nothing aborts and the outcome
+//    is the serial execution in transaction-id order (Sec. II-C GPUTx;
+//    Sec. III-E.3 access tables).  Commit order: transaction id.
+//
+// A workload policy `Work` supplies the record layout:
+//   valid_txn(a, tx), valid_op(a, d), rec(a, d) (control word, or NO_CC),
+//   writes(d), load(a, d), compute(a, d, old, operand), store(a, d, new),
+//   commit_step(a, L, S, t, first, nops) (work after commit, e.g. inserts).
+#pragma once
+
+#include "engine.cuh"
+
+namespace gcc {
+
+constexpr uint32_t NO_CC = 0xffffffffu;     // an op on data that never changes
+
+__device__ __forceinline__ uint32_t op_key(uint64_t d) { return (uint32_t)d; }
+__device__ __forceinline__ uint32_t op_field(uint64_t d) { return (uint32_t)(d >> 32) & 0xffu; }
+__device__ __forceinline__ uint32_t op_kind(uint64_t d) { return (uint32_t)(d >> 40) & 0xffu; }
+
+struct Stage {
+    uint64_t* desc;
+    uint64_t* obs;
+    ulonglong2* oldv;
+    ulonglong2* newv;
+};
+
+struct Lane {
+    uint32_t lane, lig, G, gbase;
+    unsigned gmask;
+};
+
+enum { ABORT = 0, COMMIT = 1, GIVE_UP = 2 };
+
+__device__ __forceinline__ bool collapse_loser(const ExecArgs& a, uint32_t rec) {
+    if (a.collapse != 1) return false;
+    const unsigned am = __activemask();
+    const unsigned peers = __match_any_sync(am, rec);
+    return (peers & lanemask_lt()) != 0;
+}
+
+__device__ __forceinline__ bool injected_abort(const ExecArgs& a, uint32_t t, uint32_t attempt) {
+    if (a.inject_ppm == 0) return false;
+    const uint64_t h = mix64(a.seed ^ (0x9E3779B97F4A7C15ull * (t + 1)) ^ ((uint64_t)attempt << 40));
+    return (uint32_t)(h % 1000000ull) < a.inject_ppm;
+}
+
+__device__ __forceinline__ unsigned long long group_ticket(const Lane& L, unsigned long long* ctr) {
+    unsigned long long v = 0;
+    if (L.lig == 0) v = agg_ticket(ctr);
+    return __shfl_sync(L.gmask, v, L.gbase);
+}
+
+// ---------------------------------------------------------------------------
+// OCC
+// ---------------------------------------------------------------------------
+template <class Work>
+__device__ int occ_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint32_t t,
+                           uint64_t first, uint32_t nops, uint32_t attempt,
+                           unsigned long long& order_key) {
+    const uint32_t kmax = (nops + L.G - 1) / L.G;
+    bool fail = false;
+    // read phase: consistent (version, value) pairs into the workspace
+    for (uint32_t k = 0; k < kmax; ++k) {
+        const uint32_t j = L.lig + k * L.G;
+        if (j < nops) {
+            const uint64_t d = S.desc[j];
+            const uint32_t r = Work::rec(a, d);
+            if (r == NO_CC) {
+                S.oldv[j] = Work::load(a, d);
+            } else {
+                uint64_t* m = a.meta + r;
+                for (uint32_t tries = 0;; ++tries) {
+                    const uint64_t v1 = ld_acquire(m);
+                    if (!(v1 & OCC_LOCK)) {
+                        const ulonglong2 v = Work::load(a, d);
+                        __threadfence();
+                        if (ld_relaxed(m) == v1) {
+                            S.obs[j] = v1;
+                            S.oldv[j] = v;
+                            if (Work::writes(d))
+                                S.newv[j] = Work::compute(a, d, v, a.operands[first + j]);
+                            break;
+                        }
+                    }
+                    if (tries >= a.read_retries) { fail = true; break; }
+                }
+            }
+        }
+        if (__any_sync(L.gmask, fail)) return ABORT;
+    }
+    // lock the write set, no waiting; a changed version fails the CAS too
+    uint64_t held = 0;
+    for (uint32_t k = 0; k < kmax; ++k) {
+        const uint32_t j = L.lig + k * L.G;
+        if (j < nops && Work::writes(S.desc[j])) {
+            const uint32_t r = Work::rec(a, S.desc[j]);
+            bool ok = !collapse_loser(a, r);
+            if (ok) ok = cas64(a.meta + r, S.obs[j], S.obs[j] | OCC_LOCK) == S.obs[j];
+            if (ok) held |= 1ull << k; else fail = true;
+        }
+        if (__any_sync(L.gmask, fail)) break;
+    }
+    fail = __any_sync(L.gmask, fail) || injected_abort(a, t, attempt);
+    if (!fail) {
+        __threadfence();
+        const unsigned long long ts = group_ticket(L, &a.dbs->occ_clock);
+        // validate the read set against the versions observed
+        for (uint32_t k = 0; k < kmax; ++k) {
+            const uint32_t j = L.lig + k * L.G;
+            if (j < nops && !Work::writes(S.desc[j])) {
+                const uint32_t r = Work::rec(a, S.desc[j]);
+                if (r != NO_CC && ld_relaxed(a.meta + r) != S.obs[j]) fail = true;
+            }
+        }
+        if (!__any_sync(L.gmask, fail)) {
+            // write phase, then publish the new version and unlock
+            for (uint32_t k = 0; k < kmax; ++k)
+                if (held >> k & 1) {
+                    const uint32_t j = L.lig + k * L.G;
+                    Work::store(a, S.desc[j], S.newv[j], first + j);
+                }
+            __threadfence();
+            for (uint32_t k = 0; k < kmax; ++k)
+                if (held >> k & 1)
+                    st_relaxed(a.meta + Work::rec(a, S.desc[L.lig + k * L.G]), ts + 1);
+            order_key = ts;
+            return COMMIT;
+        }
+    }
+    for (uint32_t k = 0; k < kmax; ++k)
+        if (held >> k & 1) {
+            const uint32_t j = L.lig + k * L.G;
+            st_release(a.meta + Work::rec(a, S.desc[j]), S.obs[j]);
+        }
+    return ABORT;
+}
+
+// ---------------------------------------------------------------------------
+// NO_WAIT 2PL
+// ---------------------------------------------------------------------------
+template <class Work>
+__device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint32_t t,
+                           uint64_t first, uint32_t nops, uint32_t attempt,
+                           unsigned long long& order_key) {
+    const uint32_t kmax = (nops + L.G - 1) / L.G;
+    bool fail = false;
+    uint64_t held = 0;
+    for (uint32_t k = 0; k < kmax; ++k) {
+        const uint32_t j = L.lig + k * L.G;
+        if (j < nops) {
+            const uint64_t d = S.desc[j];
+            const uint32_t r = Work::rec(a, d);
+            if (r != NO_CC) {
+                uint64_t* m = a.meta + r;
+                if (!Work::writes(d)) {
+                    for (uint32_t tries = 0;; ++tries) {
+                        const uint64_t w = ld_relaxed(m);
+                        if (w & TPL_X) { fail = true; break; }
+                        if (cas64(m, w, w + TPL_S_ONE) == w) { held |= 1ull << k; break; }
+                        if (tries >= a.read_retries) { fail = true; break; }
+                    }
+                } else {
+                    bool ok = !collapse_loser(a, r);
+                    if (ok) ok = cas64(m, 0ull, TPL_X | (uint64_t)(t + 1)) == 0ull;
+                    if (ok) held |= 1ull << k; else fail = true;
+                }
+                if (!fail) __threadfence();
+            }
+            if (!fail) {
+                const ulonglong2 v = Work::load(a, d);
+                S.oldv[j] = v;
+                if (Work::writes(d)) S.newv[j] = Work::compute(a, d, v, a.operands[first + j]);
+            }
+        }
+        if (__any_sync(L.gmask, fail)) break;
+    }
+    fail = __any_sync(L.gmask, fail) || injected_abort(a, t, attempt);
+    if (!fail) {
+        // lock point: every lock is held
+        const unsigned long long ts = group_ticket(L, &a.st->ticket);
+        for (uint32_t k = 0; k < kmax; ++k)
+            if (held >> k & 1) {
+                const uint32_t j = L.lig + k * L.G;
+                if (Work::writes(S.desc[j])) Work::store(a, S.desc[j], S.newv[j], first + j);
+            }
+        __threadfence();
+        order_key = ts;
+    }
+    for (uint32_t k = 0; k < kmax; ++k)
+        if (held >> k & 1) {
+            const uint32_t j = L.lig + k * L.G;
+            uint64_t* m = a.meta + Work::rec(a, S.desc[j]);
+            if (!Work::writes(S.desc[j])) add64(m, (uint64_t)0 - TPL_S_ONE);
+            else st_release(m, 0ull);
+        }
+    return fail ? ABORT : COMMIT;
+}
+
+// ---------------------------------------------------------------------------
+// basic TO
+// ---------------------------------------------------------------------------
+template <class Work>
+__device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint32_t t,
+                          uint64_t first, uint32_t nops, uint32_t attempt,
+                          unsigned long long& order_key) {
+    const uint32_t kmax = (nops + L.G - 1) / L.G;
+    const unsigned long long ts = group_ticket(L, &a.st->ticket) + 1;
+    if (ts > TO_TS_MASK) {
+        if (L.lig == 0) atomicOr(&a.st->error, GCC_DEVERR_TS_OVERFLOW);
+        return GIVE_UP;
+    }
+    bool fail = false;
+    uint64_t held = 0;
+    for (uint32_t k = 0; k < kmax; ++k) {
+        const uint32_t j = L.lig + k * L.G;
+        if (j < nops) {
+            const uint64_t d = S.desc[j];
+            const uint32_t r = Work::rec(a, d);
+            uint64_t* m = a.meta + (r == NO_CC ? 0 : r);
+            if (r == NO_CC) {
+                S.oldv[j] = Work::load(a, d);
+            } else if (!Work::writes(d)) {
+                for (uint32_t tries = 0;; ++tries) {
+                    const uint64_t w = ld_acquire(m);
+                    const uint64_t wts = w & TO_TS_MASK, rts = (w >> TO_RTS_SHIFT) & TO_TS_MASK;
+                    if ((w & TO_DIRTY) || ts < wts) { fail = true; break; }
+                    const ulonglong2 v = Work::load(a, d);
+                    __threadfence();
+                    bool ok;
+                    if (rts >= ts) {
+                        ok = ld_relaxed(m) == w;
+                    } else {
+                        const uint64_t nw = (w & ~(TO_TS_MASK << TO_RTS_SHIFT)) | (ts << TO_RTS_SHIFT);
+                        ok = cas64(m, w, nw) == w;
+                    }
+                    if (ok) { S.oldv[j] = v; break; }
+                    if (tries >= a.read_retries) { fail = true; break; }
+                }
+            } else {
+                bool ok = !collapse_loser(a, r);
+                for (uint32_t tries = 0; ok; ++tries) {
+                    const uint64_t w = ld_relaxed(m);
+                    const uint64_t wts = w & TO_TS_MASK, rts = (w >> TO_RTS_SHIFT) & TO_TS_MASK;
+                    if ((w & TO_DIRTY) || ts < rts || ts < wts) { ok = false; break; }
+                    const uint64_t nw = TO_DIRTY | (rts << TO_RTS_SHIFT) | ts;
+                    if (cas64(m, w, nw) == w) { S.obs[j] = w; break; }
+                    if (tries >= a.read_retries) { ok = false; break; }
+                }
+                if (ok) {
+                    held |= 1ull << k;
+                    __threadfence();
+                    const ulonglong2 v = Work::load(a, d);
+                    S.oldv[j] = v;
+                    S.newv[j] = Work::compute(a, d, v, a.operands[first + j]);
+                } else {
+                    fail = true;
+                }
+            }
+        }
+        if (__any_sync(L.gmask, fail)) break;
+    }
+    fail = __any_sync(L.gmask, fail) || injected_abort(a, t, attempt);
+    if (!fail) {
+        for (uint32_t k = 0; k < kmax; ++k)
+            if (held >> k & 1) {
+                const uint32_t j = L.lig + k * L.G;
+                Work::store(a, S.desc[j], S.newv[j], first + j);
+            }
+        __threadfence();
+        for (uint32_t k = 0; k < kmax; ++k)
+            if (held >> k & 1) {
+                const uint32_t j = L.lig + k * L.G;
+                st_relaxed(a.meta + Work::rec(a, S.desc[j]),
+                           (S.obs[j] & (TO_TS_MASK << TO_RTS_SHIFT)) | ts);
+            }
+        order_key = ts;
+        return COMMIT;
+    }
+    for (uint32_t k = 0; k < kmax; ++k)
+        if (held >> k & 1) {
+            const uint32_t j = L.lig + k * L.G;
+            st_release(a.meta + Work::rec(a, S.desc[j]), S.obs[j]);
+        }
+    return ABORT;
+}
+
+// ---------------------------------------------------------------------------
+// DET
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool det_wait(const ExecArgs& a, uint64_t* m, bool is_write,
+                                         uint32_t need) {
+    uint64_t t_begin = 0;
+    for (uint32_t spins = 0;; ++spins) {
+        const uint64_t c = ld_acquire(m);
+        const uint32_t done = is_write ? (uint32_t)(c >> 32) : (uint32_t)c;
+        if (done >= need) return true;
+        if ((spins & 31) == 31) {
+            const uint64_t now = globaltimer();
+            if (t_begin == 0) t_begin = now;
+            else if (now - t_begin > a.wait_budget_ns) {
+                atomicOr(&a.st->error, GCC_DEVERR_WAIT_BUDGET);
+                return false;
+            }
+            if (*reinterpret_cast<volatile unsigned*>(&a.st->error) &
+                (GCC_DEVERR_WAIT_BUDGET | GCC_DEVERR_DEADLINE))
+                return false;
+            __nanosleep(64);
+        }
+    }
+}
+
+template <class Work>
+__device__ int det_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint32_t t,
+                           uint64_t first, uint32_t nops, unsigned long long& order_key) {
+    const uint32_t kmax = (nops + L.G - 1) / L.G;
+    bool fail = false;
+    for (uint32_t k = 0; k < kmax && !fail; ++k) {
+        const uint32_t j = L.lig + k * L.G;
+        if (j < nops) {
+            const uint64_t d = S.desc[j];
+            const uint32_t r = Work::rec(a, d);
+            if (r == NO_CC) {
+                S.oldv[j] = Work::load(a, d);
+                continue;
+            }
+            uint64_t* m = a.meta + r;
+            const bool w = Work::writes(d);
+            if (!det_wait(a, m, w, a.need[first + j])) { fail = true; break; }
+            const ulonglong2 v = Work::load(a, d);
+            S.oldv[j] = v;
+            if (w) Work::store(a, d, Work::compute(a, d, v, a.operands[first + j]), first + j);
+            __threadfence();
+            add64(m, w ? DET_WRITE_DONE : DET_READ_DONE);
+        }
+    }
+    if (__any_sync(L.gmask, fail)) return GIVE_UP;
+    order_key = t;
+    return COMMIT;
+}
+
+// An invalid transaction never runs, but its accesses are in the batch's
+// access table: advance its records' counters in order so that later
+// transactions on those records are not held up.
+template <class Work>
+__device__ void det_skip(const ExecArgs& a, const Lane& L, uint64_t first, uint32_t nops) {
+    if (first + nops > a.n_ops) return;
+    for (uint32_t j = L.lig; j < nops; j += L.G) {
+        const uint64_t d = a.ops[first + j];
+        const uint32_t rec = cc_record(d, Work::SCHEMA, a.n_warehouses, NO_CC);
+        if (rec >= a.n_meta) continue;
+        const bool w = kind_writes(op_kind(d));
+        if (det_wait(a, a.meta + rec, w, a.need[first + j]))
+            add64(a.meta + rec, w ? DET_WRITE_DONE : DET_READ_DONE);
+    }
+}
+
+// Rounds an aborted transaction sits out: uniform in [0, window], the window
+// doubling with each abort up to backoff_cap_ns / backoff_base_ns.
+__device__ __forceinline__ uint32_t backoff_rounds(const ExecArgs& a, uint32_t t, uint32_t attempts) {
+    if (a.backoff_base_ns == 0) return 0;
+    uint64_t cap = a.backoff_cap_ns / a.backoff_base_ns;
+    if (cap < 1) cap = 1;
+    const uint32_t sh = attempts - 1 < 20 ? attempts - 1 : 20;
+    uint64_t window = 1ull << sh;
+    if (window > cap) window = cap;
+    return (uint32_t)(mix64(a.seed ^ ((uint64_t)t << 24) ^ attempts) % (window + 1));
+}
+
+// ---------------------------------------------------------------------------
+// the persistent kernel
+// ---------------------------------------------------------------------------
+template <int SCHEME, class Work>
+__global__ void __launch_bounds__(1024) exec_kernel(const ExecArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    Lane L;
+    L.G = a.lanes;
+    L.lane = threadIdx.x & 31;
+    L.lig = L.lane & (L.G - 1);
+    L.gbase = L.lane & ~(L.G - 1);
+    L.gmask = (L.G == 32) ? 0xffffffffu : (((1u << L.G) - 1u) << L.gbase);
+    const uint32_t slots = blockDim.x / L.G;
+    const uint32_t slot = threadIdx.x / L.G;
+    const uint32_t M = a.max_ops;
+    Stage S;
+    uint64_t* w64 = reinterpret_cast<uint64_t*>(smem);
+    S.desc = w64 + (size_t)slot * M;
+    S.obs = w64 + (size_t)slots * M + (size_t)slot * M;
+    ulonglong2* w128 = reinterpret_cast<ulonglong2*>(w64 + 2 * (size_t)slots * M);
+    S.oldv = w128 + (size_t)slot * M;
+    S.newv = w128 + (size_t)slots * M + (size_t)slot * M;
+
+    constexpr bool DENSE = SCHEME == GCC_NO_WAIT_2PL || SCHEME == GCC_DET;
+    const uint64_t deadline = globaltimer() + a.deadline_ns;
+    unsigned commits = 0, aborts = 0, timeouts = 0, invalid = 0, max_att = 0;
+    bool finished = false, has = false;
+    uint32_t t = 0, nops = 0, attempts = 0, wait = 0;
+    uint64_t first = 0;
+
+    for (;;) {
+        // 1. groups without a transaction take the next one
+        if (!has && !finished) {
+            unsigned long long tt = 0;
+            if (L.lig == 0) tt = agg_ticket(&a.st->fetch);
+            tt = __shfl_sync(L.gmask, tt, L.gbase);
+            if (tt >= a.n_txns) {
+                finished = true;
+            } else {
+                t = (uint32_t)tt;
+                const gcc_txn tx = a.txns[t];  // broadcast load
+                nops = tx.n_ops;
+                first = tx.first_op;
+                bool bad = nops > M || !Work::valid_txn(a, tx) || first + nops > a.n_ops;
+                if (!bad) {
+                    for (uint32_t j = L.lig; j < nops; j += L.G) {
+                        const uint64_t d = a.ops[first + j];
+                        S.desc[j] = d;
+                        if (!Work::valid_op(a, d)) bad = true;
+                    }
+                }
+                __syncwarp(L.gmask);
+                if (!__any_sync(L.gmask, bad)) {
+                    // keys of one transaction must be distinct records
+                    for (uint32_t j = L.lig; j < nops; j += L.G) {
+                        const uint32_t rj = Work::rec(a, S.desc[j]);
+                        if (rj == NO_CC) continue;
+                        for (uint32_t i = 0; i < j; ++i)
+                            if (Work::rec(a, S.desc[i]) == rj) bad = true;
+                    }
+                    bad = bad || !Work::valid_shape(a, S, nops, tx.type);
+                }
+                if (__any_sync(L.gmask, bad)) {
+                    if constexpr (SCHEME == GCC_DET) det_skip<Work>(a, L, first, nops);
+                    if (L.lig == 0) {
+                        a.results[t] = gcc_txn_result{GCC_TXN_INVALID, 0u, ~0ull};
+                        if (!DENSE) a.order_key[t] = ~0ull;
+                        atomicOr(&a.st->error, GCC_DEVERR_INVALID);
+                        ++invalid;
+                    }
+                } else {
+                    has = true;
+                    attempts = 0;
+                    wait = 0;
+                }
+                __syncwarp(L.gmask);
+            }
+        }
+        if (__all_sync(0xffffffffu, finished)) break;
+
+        // 2. one attempt per group holding a transaction and not backing off
+        const bool go = has && wait == 0;
+        if (has && wait > 0) --wait;
+        if (go) {
+            ++attempts;
+            unsigned long long order_key = 0;
+            int outcome;
+            if constexpr (SCHEME == GCC_OCC)
+                outcome = occ_attempt<Work>(a, L, S, t, first, nops, attempts, order_key);
+            else if constexpr (SCHEME == GCC_NO_WAIT_2PL)
+                outcome = tpl_attempt<Work>(a, L, S, t, first, nops, attempts, order_key);
+            else if constexpr (SCHEME == GCC_TO)
+                outcome = to_attempt<Work>(a, L, S, t, first, nops, attempts, order_key);
+            else
+                outcome = det_attempt<Work>(a, L, S, t, first, nops, order_key);
+            if (outcome == ABORT) {
+                if (L.lig == 0) ++aborts;
+                if (attempts >= a.max_attempts) {
+                    if (L.lig == 0) atomicOr(&a.st->error, GCC_DEVERR_ATTEMPTS);
+                    outcome = GIVE_UP;
+                } else if (globaltimer() > deadline) {
+                    if (L.lig == 0) atomicOr(&a.st->error, GCC_DEVERR_DEADLINE);
+                    outcome = GIVE_UP;
+                } else {
+                    wait = backoff_rounds(a, t, attempts);
+                }
+            }
+            if (outcome == COMMIT) {
+                for (uint32_t j = L.lig; j < nops; j += L.G) a.reads[first + j] = S.oldv[j];
+                Work::commit_step(a, L, S, t, first, nops);
+                if (L.lig == 0) {
+                    // 2PL tickets are dense already; OCC/TO keys are densified later
+                    a.results[t] = gcc_txn_result{GCC_TXN_COMMITTED, attempts,
+                                                  DENSE ? (uint64_t)order_key : ~0ull};
+                    if (!DENSE) a.order_key[t] = order_key;
+                    ++commits;
+                }
+            } else if (outcome == GIVE_UP) {
+                if (L.lig == 0) {
+                    a.results[t] = gcc_txn_result{GCC_TXN_TIMEOUT, attempts, ~0ull};
+                    if (!DENSE) a.order_key[t] = ~0ull;
+                    ++timeouts;
+                }
+            }
+            if (outcome != ABORT) {
+                if (L.lig == 0 && attempts > max_att) max_att = attempts;
+                has = false;
+            }
+            __syncwarp(L.gmask);
+        }
+        // 3. a warp where nobody attempted this round sleeps one quantum
+        if (!__any_sync(0xffffffffu, go)) __nanosleep(a.backoff_base_ns ? a.backoff_base_ns : 32);
+    }
+    // one atomic per warp and counter
+    commits = __reduce_add_sync(0xffffffffu, commits);
+    aborts = __reduce_add_sync(0xffffffffu, aborts);
+    timeouts = __reduce_add_sync(0xffffffffu, timeouts);
+    invalid = __reduce_add_sync(0xffffffffu, invalid);
+    max_att = __reduce_max_sync(0xffffffffu, max_att);
+    if ((threadIdx.x & 31) == 0) {
+        if (commits) atomicAdd(&a.st->committed, (unsigned long long)commits);
+        if (aborts) atomicAdd(&a.st->aborts, (unsigned long long)aborts);
+        if (timeouts) atomicAdd(&a.st->timeouts, (unsigned long long)timeouts);
+        if (invalid) atomicAdd(&a.st->invalid, (unsigned long long)invalid);
+        if (max_att) atomicMax(&a.st->max_attempts, (unsigned long long)max_att);
+    }
+}
+
+template <int SCHEME, class Work>
+cudaError_t launch_exec(const ExecArgs& a, int grid, int block, size_t smem, cudaStream_t s) {
+    auto k = exec_kernel<SCHEME, Work>;
+    if (smem > 48 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int SCHEME, class Work>
+int exec_occupancy(int block, size_t smem) {
+    auto k = exec_kernel<SCHEME, Work>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+}  // namespace gcc

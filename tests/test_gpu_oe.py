@@ -1,0 +1,88 @@
+"""GPU parity of the order-entry path (NewOrder / Payment) against the oracle.
+
+Each batch is replayed by the oracle in the reported commit order: every read
+of a committed transaction and every column of the final database (including
+the inserted orders, new-order flags and order lines) must match exactly; the
+order-entry consistency conditions must hold; the deterministic scheme must
+equal serial execution in transaction-id order.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_10158_gb300 import workload as wl
+
+pytestmark = pytest.mark.gpu
+SCHEMES = ["occ", "2pl", "to", "det"]
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_10158_gb300 import engine
+    return engine
+
+
+def run_and_check(eng, W, n_txns, scheme, seed=5, lanes=None):
+    db0, batch, cap = wl.order_entry(seed=seed, W=W, n_txns=n_txns)
+    with eng.Database("oe", n_warehouses=W, order_cap=cap, max_ops_per_txn=33,
+                      max_batch_txns=n_txns, max_batch_ops=batch.n_ops) as db:
+        db.load_oe(db0)
+        p = eng.params(lanes_per_txn=lanes) if lanes else None
+        res, reads, stats = db.run(scheme, batch, p, timeout_s=300)
+        final = db.read_oe()
+    assert stats["committed"] == n_txns and stats["device_error"] == 0, stats
+    rep = oracle.oe_replay_check(db0, final, W, cap, batch, res, reads)
+    assert rep["ok"], (scheme, rep)
+    assert oracle.oe_consistency(final, W, cap) == 0
+    if scheme == "det":
+        ref, ref_reads = oracle.oe_serial(db0, W, cap, batch)
+        assert np.array_equal(res["commit_order"], np.arange(n_txns))
+        assert all(np.array_equal(ref[c], final[c]) for c in wl.OE_COLUMNS)
+        assert np.array_equal(ref_reads, reads)
+    return stats
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("W", [1, 8])
+def test_order_entry_small(eng, scheme, W):
+    run_and_check(eng, W, 1 << 13, scheme)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_order_entry_lane_widths(eng, scheme):
+    for lanes in (1, 4, 32):
+        run_and_check(eng, 2, 4096, scheme, seed=11, lanes=lanes)
+
+
+def test_order_entry_rejects_malformed(eng):
+    W = 1
+    db0, batch, cap = wl.order_entry(seed=3, W=W, n_txns=64)
+    ops = batch.ops.copy()
+    txns = batch.txns
+    pay = np.nonzero(txns["type"] == wl.TXN_PAYMENT)[0][:2]
+    no = np.nonzero(txns["type"] == wl.TXN_NEW_ORDER)[0][:1]
+    ops["key"][txns["first_op"][pay[0]]] = W                 # warehouse out of range
+    ops["kind"][txns["first_op"][pay[1]] + 1] = wl.OE_C_PAY  # wrong op layout
+    ops["kind"][txns["first_op"][no[0]] + 3] = wl.OE_S_NEWORDER
+    bad = wl.KVBatch(txns=txns, ops=ops, operands=batch.operands)
+    with eng.Database("oe", n_warehouses=W, order_cap=cap, max_ops_per_txn=33,
+                      max_batch_txns=64, max_batch_ops=batch.n_ops) as db:
+        for scheme in SCHEMES:
+            db.load_oe(db0)
+            res, reads, stats = db.run(scheme, bad)
+            st = res["status"]
+            assert (st[[pay[0], pay[1], no[0]]] == oracle.ST_INVALID).all(), scheme
+            assert (np.delete(st, [pay[0], pay[1], no[0]]) == oracle.ST_COMMITTED).all(), scheme
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("W", [1, 8, 64])
+def test_order_entry_full_size(eng, W):
+    """2^18 txns, 50/50 NewOrder/Payment, every scheme (the paper's TPC-C shape)."""
+    for scheme in SCHEMES:
+        run_and_check(eng, W, 1 << 18, scheme, seed=wl.SEEDS[2])
