@@ -257,7 +257,7 @@ gcc_status create_impl(const gcc_db_desc* desc, gcc_db** out) {
             return bail(fail(GCC_ERR_CUDA, "cannot upload column table"));
         db->n_meta = W * (1 + OE_DIST + OE_DIST * OE_CUST) + W * OE_ITEMS;
     }
-    if ((s = dev_alloc(&db->meta, db->n_meta * 8, "control words"))) return bail(s);
+    if ((s = dev_alloc(&db->meta, db->n_meta * 16, "control words (16 bytes per record for TO)"))) return bail(s);
     if ((s = dev_alloc(&db->st, sizeof(gcc::BatchState), "batch state"))) return bail(s);
     if ((s = dev_alloc(&db->dbs, sizeof(gcc::DbState), "db state"))) return bail(s);
     const uint64_t items = std::max<uint64_t>(d.max_batch_ops, d.max_batch_txns);
@@ -319,10 +319,10 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     switch (scheme) {
         case GCC_NO_WAIT_2PL: reset = db->meta_state != META_ZERO; break;
         case GCC_OCC: reset = db->meta_state != META_ZERO && db->meta_state != META_OCC; break;
-        case GCC_TO: reset = true; break;      // timestamps are per batch
+        case GCC_TO: reset = db->meta_state != META_ZERO && db->meta_state != META_TO; break;
         case GCC_DET: reset = false; break;    // per-record counters set by preprocessing
     }
-    if (reset) GCC_CK(cudaMemsetAsync(db->meta, 0, db->n_meta * 8, st));
+    if (reset) GCC_CK(cudaMemsetAsync(db->meta, 0, db->n_meta * 16, st));
 
     gcc::ExecArgs a{};
     a.txns = d_txns;
@@ -342,7 +342,7 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     a.order_cap = db->d.order_cap;
     a.need = db->need;
     a.order_key = db->order_key;
-    a.order_key_uses_base = scheme == GCC_OCC;
+    a.order_key_uses_base = scheme == GCC_OCC || scheme == GCC_TO;
     a.st = db->st;
     a.dbs = db->dbs;
     a.lanes = p.lanes_per_txn;
@@ -489,7 +489,7 @@ gcc_status gcc_load_table(gcc_db* db, uint32_t id, const void* src, uint64_t nby
     GCC_CK(cudaDeviceSynchronize());
     GCC_CK(cudaMemcpy(table_ptr(db, id), src, nbytes,
                       src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
-    GCC_CK(cudaMemset(db->meta, 0, db->n_meta * 8));
+    GCC_CK(cudaMemset(db->meta, 0, db->n_meta * 16));
     db->meta_state = META_ZERO;
     GCC_CK(cudaDeviceSynchronize());
     return GCC_OK;

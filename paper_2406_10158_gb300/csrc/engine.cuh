@@ -22,10 +22,11 @@ constexpr uint64_t OCC_LOCK = 1ull << 63;
 // holder (transaction id + 1) -- Table II's shared bit / holder count / holder.
 constexpr uint64_t TPL_X = 1ull << 63;
 constexpr uint64_t TPL_S_ONE = 1ull << 32;
-// TO: bit 63 dirty (the commit bit of Table II), bits 31..61 RTS, bits 0..30 WTS.
+// TO: one 16-byte word per record, updated with a 128-bit CAS: lo = RTS,
+// hi = WTS (bits 0..62) | dirty (bit 63, the commit bit of Table II).  Table
+// II packs commit bit + 31-bit RTS + 31-bit WTS into 8 bytes, which overflows
+// after 2^31 attempts; 64-bit timestamps from a persistent clock never do.
 constexpr uint64_t TO_DIRTY = 1ull << 63;
-constexpr uint64_t TO_TS_MASK = (1ull << 31) - 1;
-constexpr int TO_RTS_SHIFT = 31;
 // DET: bits 32..63 ops completed on the record, bits 0..31 writes completed,
 // both counted from the record's first position in the batch's sorted
 // access table (Sec. III-E.3, "access tables").
@@ -35,8 +36,8 @@ constexpr uint64_t DET_WRITE_DONE = (1ull << 32) + 1;
 // Per-batch device state (zeroed by the batch-begin kernel).
 struct BatchState {
     unsigned long long fetch;        // next transaction id to hand out
-    unsigned long long ticket;       // 2PL commit counter / TO timestamp counter
-    unsigned long long ticket_base;  // OCC: persistent clock at batch start
+    unsigned long long ticket;       // 2PL commit counter
+    unsigned long long ticket_base;  // OCC/TO: persistent clock at batch start
     unsigned long long committed;
     unsigned long long aborts;
     unsigned long long timeouts;
@@ -49,6 +50,7 @@ struct BatchState {
 // Persistent per-database device state.
 struct DbState {
     unsigned long long occ_clock;    // OCC commit timestamps, never reset
+    unsigned long long to_clock;     // TO attempt timestamps, never reset
 };
 
 // ---------------------------------------------------------------------------
@@ -80,6 +82,21 @@ __device__ __forceinline__ ulonglong2 ld_slot16(const void* p) {
 __device__ __forceinline__ void st_slot16(void* p, ulonglong2 v) {
     asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};"
                  ::"l"(p), "l"(v.x), "l"(v.y) : "memory");
+}
+// 16-byte compare-and-swap (sm_90 and later): both halves compared and
+// replaced as one atomic operation.
+__device__ __forceinline__ ulonglong2 cas128(ulonglong2* p, ulonglong2 cmp, ulonglong2 val) {
+    ulonglong2 old;
+    asm volatile(
+        "{\n\t.reg .b128 c, v, d;\n\t"
+        "mov.b128 c, {%2, %3};\n\t"
+        "mov.b128 v, {%4, %5};\n\t"
+        "atom.relaxed.gpu.global.cas.b128 d, [%6], c, v;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t}"
+        : "=l"(old.x), "=l"(old.y)
+        : "l"(cmp.x), "l"(cmp.y), "l"(val.x), "l"(val.y), "l"(p)
+        : "memory");
+    return old;
 }
 __device__ __forceinline__ uint64_t cas64(uint64_t* p, uint64_t cmp, uint64_t val) {
     return atomicCAS(reinterpret_cast<unsigned long long*>(p), cmp, val);

@@ -241,11 +241,8 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
                           uint64_t first, uint32_t nops, uint32_t attempt,
                           unsigned long long& order_key) {
     const uint32_t kmax = (nops + L.G - 1) / L.G;
-    const unsigned long long ts = group_ticket(L, &a.st->ticket) + 1;
-    if (ts > TO_TS_MASK) {
-        if (L.lig == 0) atomicOr(&a.st->error, GCC_DEVERR_TS_OVERFLOW);
-        return GIVE_UP;
-    }
+    const unsigned long long ts = group_ticket(L, &a.dbs->to_clock) + 1;
+    ulonglong2* words = reinterpret_cast<ulonglong2*>(a.meta);
     bool fail = false;
     uint64_t held = 0;
     for (uint32_t k = 0; k < kmax; ++k) {
@@ -253,34 +250,31 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
         if (j < nops) {
             const uint64_t d = S.desc[j];
             const uint32_t r = Work::rec(a, d);
-            uint64_t* m = a.meta + (r == NO_CC ? 0 : r);
             if (r == NO_CC) {
                 S.oldv[j] = Work::load(a, d);
             } else if (!Work::writes(d)) {
+                // read: needs ts > WTS and no uncommitted write; RTS = max(RTS, ts);
+                // the CAS also proves the value read belongs to the word seen
+                ulonglong2* m = words + r;
                 for (uint32_t tries = 0;; ++tries) {
-                    const uint64_t w = ld_acquire(m);
-                    const uint64_t wts = w & TO_TS_MASK, rts = (w >> TO_RTS_SHIFT) & TO_TS_MASK;
-                    if ((w & TO_DIRTY) || ts < wts) { fail = true; break; }
+                    const ulonglong2 w = ld_slot16(m);
+                    if ((w.y & TO_DIRTY) || ts < w.y) { fail = true; break; }
                     const ulonglong2 v = Work::load(a, d);
                     __threadfence();
-                    bool ok;
-                    if (rts >= ts) {
-                        ok = ld_relaxed(m) == w;
-                    } else {
-                        const uint64_t nw = (w & ~(TO_TS_MASK << TO_RTS_SHIFT)) | (ts << TO_RTS_SHIFT);
-                        ok = cas64(m, w, nw) == w;
-                    }
-                    if (ok) { S.oldv[j] = v; break; }
+                    const ulonglong2 nw = make_ulonglong2(w.x > ts ? w.x : ts, w.y);
+                    const ulonglong2 o = cas128(m, w, nw);
+                    if (o.x == w.x && o.y == w.y) { S.oldv[j] = v; break; }
                     if (tries >= a.read_retries) { fail = true; break; }
                 }
             } else {
+                // write: needs ts > RTS and ts > WTS; mark dirty with WTS = ts
+                ulonglong2* m = words + r;
                 bool ok = !collapse_loser(a, r);
                 for (uint32_t tries = 0; ok; ++tries) {
-                    const uint64_t w = ld_relaxed(m);
-                    const uint64_t wts = w & TO_TS_MASK, rts = (w >> TO_RTS_SHIFT) & TO_TS_MASK;
-                    if ((w & TO_DIRTY) || ts < rts || ts < wts) { ok = false; break; }
-                    const uint64_t nw = TO_DIRTY | (rts << TO_RTS_SHIFT) | ts;
-                    if (cas64(m, w, nw) == w) { S.obs[j] = w; break; }
+                    const ulonglong2 w = ld_slot16(m);
+                    if ((w.y & TO_DIRTY) || ts < w.x || ts < w.y) { ok = false; break; }
+                    const ulonglong2 o = cas128(m, w, make_ulonglong2(w.x, TO_DIRTY | ts));
+                    if (o.x == w.x && o.y == w.y) { S.obs[j] = w.y; break; }
                     if (tries >= a.read_retries) { ok = false; break; }
                 }
                 if (ok) {
@@ -297,6 +291,8 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
         if (__any_sync(L.gmask, fail)) break;
     }
     fail = __any_sync(L.gmask, fail) || injected_abort(a, t, attempt);
+    // While dirty, nobody else changes a word, so only its WTS half is
+    // rewritten: the new WTS at commit, the saved one on abort.
     if (!fail) {
         for (uint32_t k = 0; k < kmax; ++k)
             if (held >> k & 1) {
@@ -305,18 +301,15 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
             }
         __threadfence();
         for (uint32_t k = 0; k < kmax; ++k)
-            if (held >> k & 1) {
-                const uint32_t j = L.lig + k * L.G;
-                st_relaxed(a.meta + Work::rec(a, S.desc[j]),
-                           (S.obs[j] & (TO_TS_MASK << TO_RTS_SHIFT)) | ts);
-            }
+            if (held >> k & 1)
+                st_relaxed(reinterpret_cast<uint64_t*>(&words[Work::rec(a, S.desc[L.lig + k * L.G])].y), ts);
         order_key = ts;
         return COMMIT;
     }
     for (uint32_t k = 0; k < kmax; ++k)
         if (held >> k & 1) {
             const uint32_t j = L.lig + k * L.G;
-            st_release(a.meta + Work::rec(a, S.desc[j]), S.obs[j]);
+            st_release(reinterpret_cast<uint64_t*>(&words[Work::rec(a, S.desc[j])].y), S.obs[j]);
         }
     return ABORT;
 }
@@ -566,11 +559,21 @@ cudaError_t launch_exec(const ExecArgs& a, int grid, int block, size_t smem, cud
 template <int SCHEME, class Work>
 int exec_occupancy(int block, size_t smem) {
     auto k = exec_kernel<SCHEME, Work>;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return 0;
+    if (smem > (size_t)optin) return 0;                  // the shape cannot launch at all
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();                              // leave no sticky error behind
+        return 0;
+    }
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     return n;
 }
 

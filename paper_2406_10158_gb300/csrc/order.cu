@@ -235,9 +235,9 @@ __global__ void dense_rank(const uint32_t* __restrict__ sk, const uint32_t* __re
     res[sv[p]].commit_order = p;
 }
 
-__global__ void batch_begin_kernel(BatchState* st, DbState* dbs) {
+__global__ void batch_begin_kernel(BatchState* st, DbState* dbs, int scheme) {
     BatchState z{};
-    z.ticket_base = dbs->occ_clock;
+    z.ticket_base = scheme == GCC_TO ? dbs->to_clock : dbs->occ_clock;
     *st = z;
 }
 
@@ -306,8 +306,8 @@ cudaError_t densify_commit_order(const ExecArgs& a, SortScratch& s, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_begin(BatchState* st, DbState* dbs, gcc_scheme, cudaStream_t s) {
-    batch_begin_kernel<<<1, 1, 0, s>>>(st, dbs);
+cudaError_t launch_batch_begin(BatchState* st, DbState* dbs, gcc_scheme scheme, cudaStream_t s) {
+    batch_begin_kernel<<<1, 1, 0, s>>>(st, dbs, (int)scheme);
     return cudaGetLastError();
 }
 

@@ -32,7 +32,9 @@ def run_and_check(eng, W, n_txns, scheme, seed=5, lanes=None):
     with eng.Database("oe", n_warehouses=W, order_cap=cap, max_ops_per_txn=33,
                       max_batch_txns=n_txns, max_batch_ops=batch.n_ops) as db:
         db.load_oe(db0)
-        p = eng.params(lanes_per_txn=lanes) if lanes else None
+        # one lane per txn stages 32 txns x 33 ops per warp: one warp per block
+        p = eng.params(lanes_per_txn=lanes, warps_per_block=1 if lanes == 1 else 8) \
+            if lanes else None
         res, reads, stats = db.run(scheme, batch, p, timeout_s=300)
         final = db.read_oe()
     assert stats["committed"] == n_txns and stats["device_error"] == 0, stats
