@@ -222,6 +222,7 @@ def run_ours(args, rank, world, dist):
     t_operands = torch.from_numpy(batch.operands.view(np.uint8).reshape(-1)).to(dev)
     t_res = torch.empty(batch.n_txns * 16, dtype=torch.uint8, device=dev)
     t_reads = torch.empty(batch.n_ops * 16, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize(dev)       # input copies done before the engine's stream runs
     kw = {}
     if args.lanes:
         kw["lanes_per_txn"] = args.lanes
