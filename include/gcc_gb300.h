@@ -293,6 +293,30 @@ gcc_status gcc_last_stats(gcc_db *db, gcc_batch_stats *stats);
 gcc_status gcc_stage_history(gcc_db *db, uint32_t max_entries, gcc_stage_times *out,
                              uint32_t *n_out);
 
+/* Deterministic (GCC_DET) execution of one key-value batch that allocates
+ * nothing.  The paper has no counterpart to this call; it exists for callers
+ * that cannot allocate device memory -- for instance a host application whose
+ * device memory is reserved up front by another framework's caching
+ * allocator, or a latency-critical loop where cudaMalloc's implicit device
+ * synchronisation is unacceptable.  The caller passes device pointers to the
+ * table (field-major slots as in gcc_load_table, updated in place), the batch
+ * and the outputs; the result equals gcc_execute with GCC_DET on a database
+ * holding the same table.  All scratch lives in one static device array of
+ * about 1.8 MB, which every GPU that loads this library keeps until the
+ * process exits.  Limits: n_records, n_ops and n_txns at most 65536 each
+ * (GCC_ERR_CAPACITY beyond), max_ops_per_txn in 1..64.  The first call on a
+ * device looks up the array's device address; make that first call before
+ * any stream capture.  Every call reuses the same array, so calls that
+ * overlap on the GPU (other streams, other host threads) race with each
+ * other.  The call only enqueues work on `stream` (NULL = legacy default
+ * stream); per-transaction outcomes land in d_results. */
+gcc_status gcc_det_execute_noalloc(void *d_table, uint32_t n_records, uint32_t n_fields,
+                                   uint32_t field_bytes, const gcc_txn *d_txns, uint32_t n_txns,
+                                   const gcc_op *d_ops, const gcc_operand *d_operands,
+                                   uint32_t n_ops, uint32_t max_ops_per_txn,
+                                   gcc_txn_result *d_results, gcc_operand *d_reads,
+                                   void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *gcc_last_error(void);
 

@@ -445,6 +445,10 @@ void fill_stats(const gcc::BatchState& h, gcc_scheme scheme, uint64_t n_txns,
 
 }  // namespace
 
+namespace gcc {
+gcc_status set_error(gcc_status s, const char* msg) { return fail(s, "%s", msg); }
+}  // namespace gcc
+
 extern "C" {
 
 const char* gcc_last_error(void) { return g_err.c_str(); }

@@ -255,6 +255,9 @@ struct DetPrep {
 cudaError_t det_prepare(const ExecArgs& a, SortScratch& s, uint32_t* scan_tmp, int key_bits,
                         int schema, cudaStream_t st);
 
+// Record `msg` as this thread's gcc_last_error() and return `s`.
+gcc_status set_error(gcc_status s, const char* msg);
+
 // OCC / TO: replace raw commit timestamps by dense ranks 0..committed-1.
 cudaError_t densify_commit_order(const ExecArgs& a, SortScratch& s, cudaStream_t st);
 

@@ -103,6 +103,9 @@ SIGNATURES = {
                                    ctypes.POINTER(ExecParams), P, P, P]),
     "gcc_last_stats": (ctypes.c_int, [P, ctypes.POINTER(BatchStats)]),
     "gcc_stage_history": (ctypes.c_int, [P, ctypes.c_uint32, P, ctypes.POINTER(ctypes.c_uint32)]),
+    "gcc_det_execute_noalloc": (ctypes.c_int, [P, ctypes.c_uint32, ctypes.c_uint32,
+                                               ctypes.c_uint32, P, ctypes.c_uint32, P, P,
+                                               ctypes.c_uint32, ctypes.c_uint32, P, P, P]),
     "gcc_last_error": (ctypes.c_char_p, []),
 }
 
