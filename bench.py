@@ -45,7 +45,9 @@ def parse_args(argv=None):
     p.add_argument("--lanes", type=int, default=0, help="lanes per transaction (0 = default)")
     p.add_argument("--warps", type=int, default=0, help="warps per block (0 = default)")
     p.add_argument("--no-schemes", action="store_true", help="skip the per-scheme lines")
-    p.add_argument("--scheme-steps", type=int, default=5)
+    p.add_argument("--scheme-steps", type=int, default=3)
+    p.add_argument("--scheme-deadline-s", type=float, default=20.0,
+                   help="kernel deadline for the per-scheme lines")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -230,24 +232,26 @@ def run_ours(args, rank, world, dist):
         kw["warps_per_block"] = args.warps
     prm = eng.params(**kw)
 
-    def step(scheme):
+    prm_sweep = eng.params(**kw, deadline_ns=int(args.scheme_deadline_s * 1e9))
+
+    def step(scheme, p=None):
         db.execute(scheme, t_txns, t_ops, t_operands, batch.n_txns, batch.n_ops, t_res, t_reads,
-                   prm, sh)
+                   p or prm, sh)
 
     def barrier():
         torch.cuda.synchronize(dev)
         if dist is not None:
             dist.barrier()
 
-    def timed(scheme, steps, warmup):
+    def timed(scheme, steps, warmup, p=None):
         for _ in range(warmup):
-            step(scheme)
+            step(scheme, p)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
-            step(scheme)
+            step(scheme, p)
         e1.record(stream)
         barrier()
         ms = e0.elapsed_time(e1)
@@ -271,7 +275,7 @@ def run_ours(args, rank, world, dist):
         schemes = {}
         if not args.no_schemes:
             for s in SCHEMES:
-                sms, shist, sst = timed(s, args.scheme_steps, 1)
+                sms, shist, sst = timed(s, args.scheme_steps, 1, prm_sweep)
                 schemes[s] = {
                     "committed_txn_per_s": sst["committed"] * args.scheme_steps / (sms / 1000.0),
                     "abort_rate": sst["abort_rate"], "ms_per_batch": sms / args.scheme_steps,

@@ -169,6 +169,11 @@ typedef struct gcc_exec_params {
                                   with this probability per million [0] */
     uint32_t immediate_restart;/* 1 = restart an aborted transaction at once, with
                                   no delay (the paper's policy) [0] */
+    uint32_t det_dataflow;     /* GCC_DET on key-value batches: 0 = evaluate each
+                                  record's chain by prefix sums [default]; 1 = run
+                                  op by op, each op waiting for its predecessors
+                                  (order-entry batches always run op by op) */
+    uint32_t reserved;         /* 0 */
 } gcc_exec_params;
 
 typedef struct gcc_batch_stats {

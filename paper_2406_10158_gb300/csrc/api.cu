@@ -90,6 +90,8 @@ struct gcc_db {
     uint32_t* scan_tmp = nullptr;
     uint32_t* need = nullptr;
     unsigned long long* order_key = nullptr;
+    uint32_t* fold_flags = nullptr;     // deterministic fold: 2 words per transaction
+    void* fold_seg = nullptr;           // deterministic fold: tile carries
     // latest execution
     cudaStream_t last_stream = nullptr;
     gcc_scheme last_scheme = GCC_OCC;
@@ -151,6 +153,7 @@ gcc_exec_params merged(const gcc_exec_params* in) {
     if (in->deadline_ns) p.deadline_ns = in->deadline_ns;
     if (in->seed) p.seed = in->seed;
     p.inject_abort_ppm = in->inject_abort_ppm;
+    p.det_dataflow = in->det_dataflow;
     return p;
 }
 
@@ -193,6 +196,8 @@ void free_db(gcc_db* db) {
     cudaFree(db->scan_tmp);
     cudaFree(db->need);
     cudaFree(db->order_key);
+    cudaFree(db->fold_flags);
+    cudaFree(db->fold_seg);
     if (db->h_states) cudaFreeHost(db->h_states);
     for (auto& r : db->stages)
         for (auto& e : r.ev)
@@ -272,6 +277,11 @@ gcc_status create_impl(const gcc_db_desc* desc, gcc_db** out) {
     if ((s = dev_alloc(&db->scan_tmp, gcc::scan_tmp_words(items) * 4, "scan scratch"))) return bail(s);
     if ((s = dev_alloc(&db->need, d.max_batch_ops * 4, "wait thresholds"))) return bail(s);
     if ((s = dev_alloc(&db->order_key, d.max_batch_txns * 8, "commit keys"))) return bail(s);
+    if (d.schema == GCC_SCHEMA_KV) {
+        if ((s = dev_alloc(&db->fold_flags, d.max_batch_txns * 8, "fold flags"))) return bail(s);
+        if ((s = dev_alloc(&db->fold_seg, gcc::fold_seg_bytes(d.max_batch_ops), "fold carries")))
+            return bail(s);
+    }
     db->n_h_states = 256;
     if (cudaMallocHost(&db->h_states, sizeof(gcc::BatchState) * db->n_h_states) != cudaSuccess)
         return bail(fail(GCC_ERR_NOMEM, "cannot allocate pinned batch states"));
@@ -360,6 +370,28 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     GCC_CK(gcc::launch_batch_begin(db->st, db->dbs, scheme, st));
     launches += 1;
     const bool kv = db->d.schema == GCC_SCHEMA_KV;
+    // deterministic key-value batches: every record chain by prefix sums
+    const bool fold = scheme == GCC_DET && kv && !p.det_dataflow;
+    if (fold) {
+        GCC_CK(cudaEventRecord(rec.ev[1], st));
+        GCC_CK(gcc::det_fold_kv(a, db->d.field_bytes, db->sort, db->scan_tmp, db->fold_flags,
+                                db->fold_seg, st));
+        const int bits = bit_length((uint64_t)db->d.n_fields * db->d.n_records);
+        launches += 2 + 3 * ((bits + 7) / 8) + 4 + 1 + 3 + 2;
+        GCC_CK(cudaEventRecord(rec.ev[2], st));
+        GCC_CK(cudaEventRecord(rec.ev[3], st));
+        rec.stream = st;
+        rec.scheme = scheme;
+        rec.n_txns = n_txns;
+        rec.launches = launches;
+        rec.grid = 0;
+        rec.used = true;
+        db->n_stages++;                  // control words untouched
+        db->last_stream = st;
+        db->last_scheme = scheme;
+        db->last_n_txns = n_txns;
+        return GCC_OK;
+    }
     if (scheme == GCC_DET && n_ops) {
         const int bits = std::max(1, kv ? bit_length(db->n_meta - 1) : bit_length(db->n_meta));
         GCC_CK(gcc::det_prepare(a, db->sort, db->scan_tmp, bits, db->d.schema, st));

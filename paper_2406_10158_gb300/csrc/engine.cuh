@@ -18,10 +18,14 @@ namespace gcc {
 // OCC: bit 63 lock, bits 0..62 version = commit timestamp + 1 (Sec. III-E.2,
 // "lock bit : 1, ts : 63").
 constexpr uint64_t OCC_LOCK = 1ull << 63;
-// 2PL: bit 63 exclusive, bits 32..62 shared-holder count, bits 0..31 exclusive
-// holder (transaction id + 1) -- Table II's shared bit / holder count / holder.
+// 2PL: bit 63 exclusive, bit 62 writer pending, bits 32..61 shared-holder
+// count, bits 0..31 exclusive holder (transaction id + 1) -- Table II's
+// shared bit / holder count / holder plus one bit that refuses new shared
+// locks while a writer is blocked by readers (nobody waits either way).
 constexpr uint64_t TPL_X = 1ull << 63;
+constexpr uint64_t TPL_PENDING = 1ull << 62;
 constexpr uint64_t TPL_S_ONE = 1ull << 32;
+constexpr uint64_t TPL_S_MASK = ((1ull << 30) - 1) << 32;
 // TO: one 16-byte word per record, updated with a 128-bit CAS: lo = RTS,
 // hi = WTS (bits 0..62) | dirty (bit 63, the commit bit of Table II).  Table
 // II packs commit bit + 31-bit RTS + 31-bit WTS into 8 bytes, which overflows
@@ -100,6 +104,15 @@ __device__ __forceinline__ ulonglong2 cas128(ulonglong2* p, ulonglong2 cmp, ulon
 }
 __device__ __forceinline__ uint64_t cas64(uint64_t* p, uint64_t cmp, uint64_t val) {
     return atomicCAS(reinterpret_cast<unsigned long long*>(p), cmp, val);
+}
+__device__ __forceinline__ uint64_t max64(uint64_t* p, uint64_t v) {
+    return atomicMax(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+__device__ __forceinline__ uint64_t and64(uint64_t* p, uint64_t v) {
+    return atomicAnd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+__device__ __forceinline__ uint64_t or64(uint64_t* p, uint64_t v) {
+    return atomicOr(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
 __device__ __forceinline__ uint64_t add64(uint64_t* p, uint64_t v) {
     return atomicAdd(reinterpret_cast<unsigned long long*>(p), v);
@@ -257,6 +270,12 @@ cudaError_t det_prepare(const ExecArgs& a, SortScratch& s, uint32_t* scan_tmp, i
 
 // Record `msg` as this thread's gcc_last_error() and return `s`.
 gcc_status set_error(gcc_status s, const char* msg);
+
+// Deterministic scheme on a key-value batch by segmented prefix sums; `flags`
+// holds 2 * n_txns words, `seg_tmp` fold_seg_bytes(n_ops) bytes.
+size_t fold_seg_bytes(size_t max_ops);
+cudaError_t det_fold_kv(const ExecArgs& a, uint32_t field_bytes, SortScratch& s,
+                        uint32_t* scan_tmp, uint32_t* flags, void* seg_tmp, cudaStream_t st);
 
 // OCC / TO: replace raw commit timestamps by dense ranks 0..committed-1.
 cudaError_t densify_commit_order(const ExecArgs& a, SortScratch& s, cudaStream_t st);

@@ -192,13 +192,24 @@ __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
                 if (!Work::writes(d)) {
                     for (uint32_t tries = 0;; ++tries) {
                         const uint64_t w = ld_relaxed(m);
-                        if (w & TPL_X) { fail = true; break; }
+                        if (w & (TPL_X | TPL_PENDING)) { fail = true; break; }
                         if (cas64(m, w, w + TPL_S_ONE) == w) { held |= 1ull << k; break; }
                         if (tries >= a.read_retries) { fail = true; break; }
                     }
                 } else {
                     bool ok = !collapse_loser(a, r);
-                    if (ok) ok = cas64(m, 0ull, TPL_X | (uint64_t)(t + 1)) == 0ull;
+                    if (ok) {
+                        const uint64_t w = ld_relaxed(m);
+                        if (w & TPL_X) {
+                            ok = false;
+                        } else if (w & TPL_S_MASK) {
+                            // blocked by readers only: hold off new readers
+                            if (!(w & TPL_PENDING)) or64(m, TPL_PENDING);
+                            ok = false;
+                        } else {
+                            ok = cas64(m, w, TPL_X | (uint64_t)(t + 1)) == w;
+                        }
+                    }
                     if (ok) held |= 1ull << k; else fail = true;
                 }
                 if (!fail) __threadfence();
@@ -253,17 +264,22 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
             if (r == NO_CC) {
                 S.oldv[j] = Work::load(a, d);
             } else if (!Work::writes(d)) {
-                // read: needs ts > WTS and no uncommitted write; RTS = max(RTS, ts);
-                // the CAS also proves the value read belongs to the word seen
+                // read: needs ts > WTS and no uncommitted write, then RTS =
+                // max(RTS, ts).  RTS only grows, so a 64-bit atomicMax raises it
+                // without failing; the WTS half read unchanged before the value
+                // and after the raise proves the value belongs to that WTS, and
+                // a writer's 128-bit CAS fails once RTS moved.
                 ulonglong2* m = words + r;
+                uint64_t* wts_word = reinterpret_cast<uint64_t*>(&m->y);
+                uint64_t* rts_word = reinterpret_cast<uint64_t*>(&m->x);
                 for (uint32_t tries = 0;; ++tries) {
-                    const ulonglong2 w = ld_slot16(m);
-                    if ((w.y & TO_DIRTY) || ts < w.y) { fail = true; break; }
+                    const uint64_t y1 = ld_acquire(wts_word);
+                    if ((y1 & TO_DIRTY) || ts < y1) { fail = true; break; }
                     const ulonglong2 v = Work::load(a, d);
                     __threadfence();
-                    const ulonglong2 nw = make_ulonglong2(w.x > ts ? w.x : ts, w.y);
-                    const ulonglong2 o = cas128(m, w, nw);
-                    if (o.x == w.x && o.y == w.y) { S.oldv[j] = v; break; }
+                    if (ld_relaxed(rts_word) < ts) max64(rts_word, ts);
+                    __threadfence();
+                    if (ld_relaxed(wts_word) == y1) { S.oldv[j] = v; break; }
                     if (tries >= a.read_retries) { fail = true; break; }
                 }
             } else {
@@ -514,6 +530,13 @@ __global__ void __launch_bounds__(1024) exec_kernel(const ExecArgs a) {
                     ++commits;
                 }
             } else if (outcome == GIVE_UP) {
+                if constexpr (SCHEME == GCC_NO_WAIT_2PL) {
+                    // drop any writer-pending marks this transaction may have set
+                    for (uint32_t j = L.lig; j < nops; j += L.G) {
+                        const uint32_t r = Work::rec(a, S.desc[j]);
+                        if (r != NO_CC && Work::writes(S.desc[j])) and64(a.meta + r, ~TPL_PENDING);
+                    }
+                }
                 if (L.lig == 0) {
                     a.results[t] = gcc_txn_result{GCC_TXN_TIMEOUT, attempts, ~0ull};
                     if (!DENSE) a.order_key[t] = ~0ull;

@@ -45,7 +45,8 @@ class ExecParams(ctypes.Structure):
                 ("max_attempts", ctypes.c_uint32), ("read_retries", ctypes.c_uint32),
                 ("wait_budget_ns", ctypes.c_uint64), ("deadline_ns", ctypes.c_uint64),
                 ("seed", ctypes.c_uint64), ("inject_abort_ppm", ctypes.c_uint32),
-                ("immediate_restart", ctypes.c_uint32)]
+                ("immediate_restart", ctypes.c_uint32), ("det_dataflow", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class BatchStats(ctypes.Structure):

@@ -12,7 +12,15 @@ import oracle
 from paper_2406_10158_gb300 import workload as wl
 
 pytestmark = pytest.mark.gpu
-SCHEMES = ["occ", "2pl", "to", "det"]
+SCHEMES = ["occ", "2pl", "to", "det", "det-dataflow"]
+
+
+def go(eng, db, scheme, batch, timeout_s=120, **kw):
+    """Run a batch; "det-dataflow" is the deterministic scheme run op by op
+    (key-value batches otherwise take the prefix-sum evaluation)."""
+    if scheme == "det-dataflow":
+        scheme, kw = "det", dict(kw, det_dataflow=1)
+    return db.run(scheme, batch, eng.params(**kw) if kw else None, timeout_s=timeout_s)
 
 
 @pytest.fixture(scope="module")
@@ -29,7 +37,7 @@ def eng():
 def check(table, final, batch, res, reads, scheme, stats=None, require_all=True):
     rep = oracle.replay_check(table, final, batch, res, reads, require_all=require_all)
     assert rep["ok"], (scheme, rep, stats)
-    if scheme == "det":
+    if scheme.startswith("det"):
         ref_final, ref_reads = oracle.serial(table, batch)
         committed = res["status"] == oracle.ST_COMMITTED
         assert committed.all()
@@ -45,7 +53,7 @@ def test_small_kv_store(eng, scheme):
     with eng.Database("kv", n_records=65536, n_fields=8, field_bytes=8,
                       max_batch_txns=4096) as db:
         db.load_kv(table)
-        res, reads, stats = db.run(scheme, batch)
+        res, reads, stats = go(eng, db, scheme, batch)
         final = db.read_kv()
     assert stats["committed"] == 4096 and stats["device_error"] == 0, stats
     check(table, final, batch, res, reads, scheme, stats)
@@ -65,8 +73,8 @@ def test_lane_group_widths(eng, scheme, lanes):
                       max_batch_txns=3000) as db:
         db.load_kv(table)
         # 1 lane per txn stages 32 txns x 40 ops per warp: keep the block small
-        res, reads, stats = db.run(scheme, batch, eng.params(lanes_per_txn=lanes,
-                                                             warps_per_block=2 if lanes == 1 else 4))
+        res, reads, stats = go(eng, db, scheme, batch, lanes_per_txn=lanes,
+                               warps_per_block=2 if lanes == 1 else 4)
         final = db.read_kv()
     assert stats["committed"] == batch.n_txns, stats
     check(table, final, batch, res, reads, scheme, stats)
@@ -82,7 +90,7 @@ def test_sixteen_byte_slots_contention(eng, scheme):
     with eng.Database("kv", n_records=nrec, n_fields=nf, field_bytes=16,
                       max_batch_txns=1 << 15) as db:
         db.load_kv(table)
-        res, reads, stats = db.run(scheme, batch)
+        res, reads, stats = go(eng, db, scheme, batch)
         final = db.read_kv()
     assert stats["committed"] == batch.n_txns, stats
     check(table, final, batch, res, reads, scheme, stats)
@@ -107,7 +115,7 @@ def test_tiny_batches_brute_force(eng, scheme):
             batch = wl.kv_batch_from_lists(lists)
             table = rng.integers(0, 1000, size=(1, 8), dtype=np.uint64)
             db.load_kv(table)
-            res, reads, stats = db.run(scheme, batch, eng.params(lanes_per_txn=1))
+            res, reads, stats = go(eng, db, scheme, batch, lanes_per_txn=1)
             final = db.read_kv()
             m, _ = oracle.brute_force(table, batch, final, reads)
             assert m >= 1, (scheme, trial)
@@ -122,11 +130,11 @@ def test_edge_cases(eng, scheme):
         db.load_kv(table)
         # empty batch
         empty = wl.kv_batch_from_lists([])
-        res, reads, stats = db.run(scheme, empty)
+        res, reads, stats = go(eng, db, scheme, empty)
         assert stats["committed"] == 0 and res.size == 0
         # read-only batch: reads are the initial values, table unchanged
         ro = wl.kv_batch(2, nrec=64, nfields=2, n_txns=16, ops_per_txn=4, read_ratio=1.0)
-        res, reads, stats = db.run(scheme, ro)
+        res, reads, stats = go(eng, db, scheme, ro)
         assert np.array_equal(db.read_kv(), table)
         assert np.array_equal(reads[:, 0], table[ro.ops["field"], ro.ops["key"]])
         # malformed transactions come back INVALID, the others commit
@@ -138,7 +146,7 @@ def test_edge_cases(eng, scheme):
             [(5, 1, 1, 7, 0)],                      # fine
         ])
         db.load_kv(table)
-        res, reads, stats = db.run(scheme, bad)
+        res, reads, stats = go(eng, db, scheme, bad)
         assert res["status"].tolist() == [3, 3, 3, 3, 1]
         assert stats["invalid"] == 4 and "invalid" in stats["errors"]
         final = db.read_kv()
@@ -147,7 +155,7 @@ def test_edge_cases(eng, scheme):
         # capacity is enforced on the host
         big = wl.kv_batch(3, nrec=64, nfields=2, n_txns=17, ops_per_txn=2)
         with pytest.raises(eng.GCCError):
-            db.submit(scheme, big)
+            db.submit("det" if scheme.startswith("det") else scheme, big)
 
 
 @pytest.mark.parametrize("scheme", ["occ", "2pl", "to"])
@@ -198,12 +206,12 @@ def test_det_wait_budget_returns(eng):
     with eng.Database("kv", n_records=nrec, n_fields=1, field_bytes=8, max_ops_per_txn=4,
                       max_batch_txns=20000) as db:
         db.load_kv(table)
-        res, reads, stats = db.run("det", batch, eng.params(wait_budget_ns=1000))
+        res, reads, stats = db.run("det", batch, eng.params(wait_budget_ns=1000, det_dataflow=1))
         if stats["device_error"]:
             assert "wait_budget" in stats["errors"]
             assert (res["status"] == oracle.ST_TIMEOUT).any()
         db.load_kv(table)
-        res, reads, stats = db.run("det", batch)
+        res, reads, stats = db.run("det", batch, eng.params(det_dataflow=1))
         check(table, db.read_kv(), batch, res, reads, "det", stats)
 
 
@@ -215,9 +223,10 @@ def test_schemes_share_one_database(eng):
     with eng.Database("kv", n_records=nrec, n_fields=4, field_bytes=8,
                       max_batch_txns=4096) as db:
         db.load_kv(state)
-        for i, scheme in enumerate(["occ", "occ", "2pl", "det", "to", "occ", "det", "2pl", "to"]):
+        for i, scheme in enumerate(["occ", "occ", "2pl", "det", "to", "occ", "det-dataflow",
+                                    "2pl", "to", "det"]):
             batch = wl.kv_batch(100 + i, nrec=nrec, nfields=4, n_txns=4096, theta=0.8)
-            res, reads, stats = db.run(scheme, batch)
+            res, reads, stats = go(eng, db, scheme, batch)
             final = db.read_kv()
             check(state, final, batch, res, reads, scheme, stats)
             state = final
@@ -235,7 +244,7 @@ def test_ycsb_full_size(eng, theta):
                       max_batch_txns=1 << 20) as db:
         db.load_kv(state)
         for scheme in SCHEMES:
-            res, reads, stats = db.run(scheme, batch, timeout_s=300)
+            res, reads, stats = go(eng, db, scheme, batch, timeout_s=300)
             final = db.read_kv()
             assert stats["committed"] == batch.n_txns, (scheme, stats)
             rep = oracle.replay_check(state, final, batch, res, reads)
@@ -253,7 +262,7 @@ def test_hot_key_zipf_099(eng, scheme):
     batch = wl.kv_batch(13, nrec=nrec, nfields=2, n_txns=4096, read_ratio=0.5, theta=0.99)
     with eng.Database("kv", n_records=nrec, n_fields=2, field_bytes=8, max_batch_txns=4096) as db:
         db.load_kv(table)
-        res, reads, stats = db.run(scheme, batch)
+        res, reads, stats = go(eng, db, scheme, batch)
         final = db.read_kv()
     assert stats["committed"] == batch.n_txns, stats
     check(table, final, batch, res, reads, scheme, stats)
