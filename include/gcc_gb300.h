@@ -157,7 +157,7 @@ typedef struct gcc_exec_params {
                                   2 = off */
     uint32_t backoff_base_ns;  /* first retry delay, doubled per abort, with
                                   random jitter [128] */
-    uint32_t backoff_cap_ns;   /* largest retry delay [65536] */
+    uint32_t backoff_cap_ns;   /* largest retry delay [1000000] */
     uint32_t max_attempts;     /* per transaction, then GCC_TXN_TIMEOUT [2^24] */
     uint32_t read_retries;     /* re-reads of a record seen mid-update before
                                   the attempt aborts [8] */
@@ -297,6 +297,82 @@ gcc_status gcc_last_stats(gcc_db *db, gcc_batch_stats *stats);
  * the streams they ran on. */
 gcc_status gcc_stage_history(gcc_db *db, uint32_t max_entries, gcc_stage_times *out,
                              uint32_t *n_out);
+
+/* Batched form: many independent key-value batches, each on its own
+ * database, executed by one persistent-kernel launch (Sec. IV-C studies the
+ * effect of launch parameters; here the launch is shared).  All databases
+ * share one device and slot width; each appears at most once.  Device
+ * pointers, as for gcc_execute. */
+typedef struct gcc_multi_batch {
+    gcc_db *db;
+    const gcc_txn *d_txns;
+    uint32_t n_txns;
+    uint32_t reserved;         /* 0 */
+    const gcc_op *d_ops;
+    const gcc_operand *d_operands;
+    uint64_t n_ops;
+    gcc_txn_result *d_results;
+    gcc_operand *d_reads;
+} gcc_multi_batch;
+
+typedef struct gcc_multi_plan gcc_multi_plan;
+
+/* Build a launch plan for `n` batches (at most 256) under OCC, NO_WAIT 2PL or
+ * TO: uploads the batch descriptors, allocates the plan's scratch (sort
+ * buffers for all transactions) and puts every database's control words in a
+ * state the scheme can start from.  The batch arrays must stay valid while
+ * the plan is used.  Synchronous. */
+gcc_status gcc_multi_plan_create(gcc_scheme scheme, const gcc_multi_batch *batches, uint32_t n,
+                                 const gcc_exec_params *params, gcc_multi_plan **out);
+
+/* Enqueue one execution of every batch of the plan on `stream` (NULL = the
+ * plan's stream): batch states reset, one persistent kernel over all
+ * transactions, commit ranks.  With use_graph != 0 the sequence is captured
+ * once into a CUDA graph (on the plan's stream) and replayed.  Allocates
+ * nothing.  Between launches, run no other scheme on the plan's databases
+ * (GCC_ERR_INVALID otherwise). */
+gcc_status gcc_multi_launch(gcc_multi_plan *plan, int use_graph, void *stream);
+
+/* Statistics of batch i of the latest launch (synchronises the device). */
+gcc_status gcc_multi_stats(gcc_multi_plan *plan, uint32_t i, gcc_batch_stats *stats);
+
+/* Free the plan (waits for its stream).  NULL is a no-op. */
+gcc_status gcc_multi_plan_destroy(gcc_multi_plan *plan);
+
+/* Launch-parameter search space for gcc_autotune.  The paper finds that the
+ * number of active lanes per warp and warps per block move throughput by up
+ * to 10x (Sec. IV-C, Exp-3 to Exp-5); this searches the engine's equivalents
+ * plus the retry-delay cap.  Zero counts take the defaults in brackets. */
+typedef struct gcc_tune_space {
+    uint32_t n_lanes;          /* [5]: lanes_per_txn in {2, 4, 8, 16, 32} */
+    uint32_t lanes[6];
+    uint32_t n_warps;          /* [4]: warps_per_block in {4, 8, 16, 32} */
+    uint32_t warps[8];
+    uint32_t n_caps;           /* [3]: backoff_cap_ns in {65536, 1000000, 16000000} */
+    uint32_t caps[4];
+    uint32_t steps;            /* timed executions per point [2] */
+    uint32_t warmup;           /* untimed executions per point [1] */
+    uint64_t point_deadline_ns;/* kernel deadline per execution [5 s] */
+} gcc_tune_space;
+
+typedef struct gcc_tune_report {
+    uint32_t points;           /* points measured (shapes that fit an SM) */
+    uint32_t best_index;       /* in measurement order */
+    double best_txn_per_s;     /* committed transactions per second at the best */
+    double default_txn_per_s;  /* the same with gcc_default_params */
+} gcc_tune_report;
+
+/* Grid search for the launch parameters that commit the given batch fastest:
+ * every point of `space` runs `warmup` + `steps` executions of the batch
+ * (device pointers, as gcc_execute) on `stream`, timed with CUDA events;
+ * *best receives the winning parameters.  The batch executes many times, so
+ * the database's contents change; tune on a copy when that matters.
+ * Synchronous. */
+gcc_status gcc_autotune(gcc_db *db, gcc_scheme scheme, const gcc_txn *d_txns, uint32_t n_txns,
+                        const gcc_op *d_ops, const gcc_operand *d_operands, uint64_t n_ops,
+                        gcc_txn_result *d_results, gcc_operand *d_reads,
+                        const gcc_tune_space *space, gcc_exec_params *best,
+                        gcc_tune_report *report, void *stream);
 
 /* Deterministic (GCC_DET) execution of one key-value batch that allocates
  * nothing.  The paper has no counterpart to this call; it exists for callers

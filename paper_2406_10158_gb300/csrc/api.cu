@@ -16,12 +16,14 @@
 #include <string>
 #include <thread>
 
-#include "engine.cuh"
+#include "runtime.cuh"
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
 
+namespace gcc {
+namespace rt {
 gcc_status fail(gcc_status st, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -40,85 +42,16 @@ gcc_status fail(gcc_status st, const char* fmt, ...) {
                         "%s failed: %s", #call, cudaGetErrorString(e_));               \
     } while (0)
 
-constexpr int OE_NCOLS = 22;
-constexpr uint32_t OE_ITEMS = 100000, OE_DIST = 10, OE_CUST = 3000, OE_LINES = 15;
+}  // namespace rt
+}  // namespace gcc
 
-// Rows of each order-entry column, in table-id order.
-uint64_t oe_rows(uint32_t col, uint64_t W, uint64_t cap) {
-    const uint64_t nd = W * OE_DIST;
-    if (col < 2) return W;                          // w_ytd, w_tax
-    if (col < 5) return nd;                         // d_ytd, d_tax, d_next_o_id
-    if (col < 9) return nd * OE_CUST;               // c_*
-    if (col < 10) return OE_ITEMS;                  // i_price
-    if (col < 14) return W * OE_ITEMS;              // s_*
-    if (col < 18) return nd * cap;                  // o_*, no_flag
-    return nd * cap * OE_LINES;                     // ol_*
-}
+using gcc::rt::fail;
+using gcc::rt::OE_NCOLS;
+using gcc::rt::oe_rows;
 
-enum MetaState { META_ZERO, META_OCC, META_TO, META_DET, META_UNKNOWN };
 
-// CUDA events bracketing the stages of one execution.
-struct StageRec {
-    cudaEvent_t ev[4] = {};        // start, before execute kernel, after it, end
-    cudaStream_t stream = nullptr;
-    uint32_t scheme = 0, n_txns = 0, launches = 0, grid = 0;
-    bool used = false;
-};
-constexpr uint32_t STAGE_RING = 256;
-
-}  // namespace
-
-struct gcc_db {
-    gcc_db_desc d{};
-    int sm_count = 0;
-    cudaStream_t stream = nullptr;
-    // key-value
-    uint8_t* table = nullptr;
-    uint64_t table_bytes = 0;
-    // order-entry
-    int64_t* cols[OE_NCOLS] = {};
-    uint64_t col_bytes[OE_NCOLS] = {};
-    int64_t** d_cols = nullptr;
-    // concurrency control
-    uint64_t* meta = nullptr;
-    uint64_t n_meta = 0;
-    gcc::BatchState* st = nullptr;
-    gcc::DbState* dbs = nullptr;
-    MetaState meta_state = META_ZERO;
-    // scratch
-    gcc::SortScratch sort{};
-    uint32_t* scan_tmp = nullptr;
-    uint32_t* need = nullptr;
-    unsigned long long* order_key = nullptr;
-    uint32_t* fold_flags = nullptr;     // deterministic fold: 2 words per transaction
-    void* fold_seg = nullptr;           // deterministic fold: tile carries
-    // latest execution
-    cudaStream_t last_stream = nullptr;
-    gcc_scheme last_scheme = GCC_OCC;
-    uint64_t last_n_txns = 0;
-    // pinned copies of BatchState for submitted batches
-    gcc::BatchState* h_states = nullptr;
-    uint32_t n_h_states = 0, next_h_state = 0;
-    // stage timing ring
-    StageRec stages[STAGE_RING];
-    uint64_t n_stages = 0;
-};
-
-struct gcc_batch {
-    gcc_db* db = nullptr;
-    cudaStream_t stream = nullptr;
-    gcc_scheme scheme = GCC_OCC;
-    uint32_t n_txns = 0;
-    uint64_t n_ops = 0;
-    void* d_in = nullptr;                 // staged inputs (host-input batches)
-    gcc_txn_result* d_results = nullptr;
-    gcc_operand* d_reads = nullptr;
-    gcc::BatchState* h_state = nullptr;   // pinned, filled at batch end
-    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
-    uint64_t stage_index = 0;             // its entry in the database's stage ring
-};
-
-namespace {
+namespace gcc {
+namespace rt {
 
 gcc_exec_params defaults() {
     gcc_exec_params p{};
@@ -127,7 +60,7 @@ gcc_exec_params defaults() {
     p.blocks_per_sm = 0;
     p.collapse = 1;
     p.backoff_base_ns = 128;
-    p.backoff_cap_ns = 65536;
+    p.backoff_cap_ns = 1000000;
     p.max_attempts = 1u << 24;
     p.read_retries = 8;
     p.wait_budget_ns = 2000000000ull;
@@ -303,6 +236,20 @@ gcc_status validate_params(const gcc_exec_params& p) {
     return GCC_OK;
 }
 
+gcc_status prepare_meta(gcc_db* db, gcc_scheme scheme, cudaStream_t st) {
+    // control words: reset whenever the previous batch left them in a state
+    // the scheme cannot start from
+    bool reset = false;
+    switch (scheme) {
+        case GCC_NO_WAIT_2PL: reset = db->meta_state != META_ZERO; break;
+        case GCC_OCC: reset = db->meta_state != META_ZERO && db->meta_state != META_OCC; break;
+        case GCC_TO: reset = db->meta_state != META_ZERO && db->meta_state != META_TO; break;
+        case GCC_DET: reset = false; break;    // per-record counters set by preprocessing
+    }
+    if (reset) GCC_CK(cudaMemsetAsync(db->meta, 0, db->n_meta * 16, st));
+    return GCC_OK;
+}
+
 gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, uint32_t n_txns,
                         const gcc_op* d_ops, const gcc_operand* d_operands, uint64_t n_ops,
                         const gcc_exec_params* params, gcc_txn_result* d_results,
@@ -323,16 +270,7 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     GCC_CK(cudaEventRecord(rec.ev[0], st));
     uint32_t launches = 0;
 
-    // control words: reset whenever the previous batch left them in a state
-    // the scheme cannot start from
-    bool reset = false;
-    switch (scheme) {
-        case GCC_NO_WAIT_2PL: reset = db->meta_state != META_ZERO; break;
-        case GCC_OCC: reset = db->meta_state != META_ZERO && db->meta_state != META_OCC; break;
-        case GCC_TO: reset = db->meta_state != META_ZERO && db->meta_state != META_TO; break;
-        case GCC_DET: reset = false; break;    // per-record counters set by preprocessing
-    }
-    if (reset) GCC_CK(cudaMemsetAsync(db->meta, 0, db->n_meta * 16, st));
+    if ((s = prepare_meta(db, scheme, st))) return s;
 
     gcc::ExecArgs a{};
     a.txns = d_txns;
@@ -475,7 +413,10 @@ void fill_stats(const gcc::BatchState& h, gcc_scheme scheme, uint64_t n_txns,
     }
 }
 
-}  // namespace
+}  // namespace rt
+}  // namespace gcc
+
+using namespace gcc::rt;
 
 namespace gcc {
 gcc_status set_error(gcc_status s, const char* msg) { return fail(s, "%s", msg); }
@@ -693,3 +634,111 @@ gcc_status gcc_batch_free(gcc_batch* b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+namespace {
+
+// Committed transactions per second of `reps` executions with params p.
+gcc_status measure_point(gcc_db* db, gcc_scheme scheme, const gcc_txn* t, uint32_t n_txns,
+                         const gcc_op* o, const gcc_operand* od, uint64_t n_ops,
+                         gcc_txn_result* r, gcc_operand* rd, const gcc_exec_params& p,
+                         uint32_t warmup, uint32_t reps, cudaStream_t st, double* rate) {
+    *rate = 0.0;
+    for (uint32_t i = 0; i < warmup; ++i) {
+        gcc_status s = execute_impl(db, scheme, t, n_txns, o, od, n_ops, &p, r, rd, st);
+        if (s) return s;
+    }
+    cudaEvent_t e0, e1;
+    GCC_CK(cudaEventCreate(&e0));
+    GCC_CK(cudaEventCreate(&e1));
+    uint64_t committed = 0;
+    gcc_status s = GCC_OK;
+    float ms = 0.f;
+    if (cudaEventRecord(e0, st) != cudaSuccess) s = fail(GCC_ERR_CUDA, "event record");
+    for (uint32_t i = 0; !s && i < reps; ++i) {
+        s = execute_impl(db, scheme, t, n_txns, o, od, n_ops, &p, r, rd, st);
+        if (!s) {
+            // each execution resets the batch state, so read it before the next
+            gcc::BatchState h{};
+            if (cudaMemcpyAsync(&h, db->st, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                s = fail(GCC_ERR_CUDA, "batch state read");
+            committed += h.committed;
+        }
+    }
+    if (!s && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        s = fail(GCC_ERR_CUDA, "event timing");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!s && ms > 0.f) *rate = (double)committed / (ms * 1e-3);
+    return s;
+}
+
+}  // namespace
+
+extern "C" gcc_status gcc_autotune(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns,
+                                   uint32_t n_txns, const gcc_op* d_ops,
+                                   const gcc_operand* d_operands, uint64_t n_ops,
+                                   gcc_txn_result* d_results, gcc_operand* d_reads,
+                                   const gcc_tune_space* space, gcc_exec_params* best,
+                                   gcc_tune_report* report, void* stream) {
+    if (!db || !best) return fail(GCC_ERR_INVALID, "null argument");
+    GCC_CK(cudaSetDevice(db->d.device));
+    gcc_tune_space sp{};
+    if (space) sp = *space;
+    static const uint32_t def_lanes[] = {2, 4, 8, 16, 32};
+    static const uint32_t def_warps[] = {4, 8, 16, 32};
+    static const uint32_t def_caps[] = {65536u, 1000000u, 16000000u};
+    if (!sp.n_lanes) { sp.n_lanes = 5; std::memcpy(sp.lanes, def_lanes, sizeof def_lanes); }
+    if (!sp.n_warps) { sp.n_warps = 4; std::memcpy(sp.warps, def_warps, sizeof def_warps); }
+    if (!sp.n_caps) { sp.n_caps = 3; std::memcpy(sp.caps, def_caps, sizeof def_caps); }
+    if (sp.n_lanes > 6 || sp.n_warps > 8 || sp.n_caps > 4)
+        return fail(GCC_ERR_INVALID, "tune space lists are too long");
+    const uint32_t steps = sp.steps ? sp.steps : 2;
+    const uint32_t warmup = sp.warmup ? sp.warmup : 1;
+    const uint64_t deadline = sp.point_deadline_ns ? sp.point_deadline_ns : 5000000000ull;
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : db->stream;
+
+    gcc_tune_report rep{};
+    gcc_exec_params dflt = defaults();
+    dflt.deadline_ns = deadline;
+    gcc_status s = measure_point(db, scheme, d_txns, n_txns, d_ops, d_operands, n_ops, d_results,
+                                 d_reads, dflt, warmup, steps, st, &rep.default_txn_per_s);
+    if (s) return s;
+    gcc_exec_params winner = dflt;
+    double best_rate = rep.default_txn_per_s;
+    for (uint32_t li = 0; li < sp.n_lanes; ++li)
+        for (uint32_t wi = 0; wi < sp.n_warps; ++wi)
+            for (uint32_t ci = 0; ci < sp.n_caps; ++ci) {
+                gcc_exec_params p = dflt;
+                p.lanes_per_txn = sp.lanes[li];
+                p.warps_per_block = sp.warps[wi];
+                p.backoff_cap_ns = sp.caps[ci];
+                if (validate_params(p)) { g_err.clear(); continue; }
+                const int block = (int)p.warps_per_block * 32;
+                const size_t smem = (size_t)(block / p.lanes_per_txn) * db->d.max_ops_per_txn *
+                                    gcc::STAGE_BYTES_PER_OP;
+                const bool kv = db->d.schema == GCC_SCHEMA_KV;
+                const int occ = kv ? gcc::kv_exec_occupancy(scheme, db->d.field_bytes, block, smem)
+                                   : gcc::oe_exec_occupancy(scheme, block, smem);
+                if (occ <= 0) continue;                          // shape does not fit
+                double rate = 0.0;
+                s = measure_point(db, scheme, d_txns, n_txns, d_ops, d_operands, n_ops, d_results,
+                                  d_reads, p, warmup, steps, st, &rate);
+                if (s) return s;
+                if (rate > best_rate) {
+                    best_rate = rate;
+                    winner = p;
+                    rep.best_index = rep.points;
+                }
+                rep.points++;
+            }
+    winner.deadline_ns = defaults().deadline_ns;
+    *best = winner;
+    rep.best_txn_per_s = best_rate;
+    if (report) *report = rep;
+    return GCC_OK;
+}

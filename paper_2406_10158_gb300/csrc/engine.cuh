@@ -18,14 +18,10 @@ namespace gcc {
 // OCC: bit 63 lock, bits 0..62 version = commit timestamp + 1 (Sec. III-E.2,
 // "lock bit : 1, ts : 63").
 constexpr uint64_t OCC_LOCK = 1ull << 63;
-// 2PL: bit 63 exclusive, bit 62 writer pending, bits 32..61 shared-holder
-// count, bits 0..31 exclusive holder (transaction id + 1) -- Table II's
-// shared bit / holder count / holder plus one bit that refuses new shared
-// locks while a writer is blocked by readers (nobody waits either way).
+// 2PL: bit 63 exclusive, bits 32..62 shared-holder count, bits 0..31 exclusive
+// holder (transaction id + 1) -- Table II's shared bit / holder count / holder.
 constexpr uint64_t TPL_X = 1ull << 63;
-constexpr uint64_t TPL_PENDING = 1ull << 62;
 constexpr uint64_t TPL_S_ONE = 1ull << 32;
-constexpr uint64_t TPL_S_MASK = ((1ull << 30) - 1) << 32;
 // TO: one 16-byte word per record, updated with a 128-bit CAS: lo = RTS,
 // hi = WTS (bits 0..62) | dirty (bit 63, the commit bit of Table II).  Table
 // II packs commit bit + 31-bit RTS + 31-bit WTS into 8 bytes, which overflows

@@ -192,24 +192,13 @@ __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
                 if (!Work::writes(d)) {
                     for (uint32_t tries = 0;; ++tries) {
                         const uint64_t w = ld_relaxed(m);
-                        if (w & (TPL_X | TPL_PENDING)) { fail = true; break; }
+                        if (w & TPL_X) { fail = true; break; }
                         if (cas64(m, w, w + TPL_S_ONE) == w) { held |= 1ull << k; break; }
                         if (tries >= a.read_retries) { fail = true; break; }
                     }
                 } else {
                     bool ok = !collapse_loser(a, r);
-                    if (ok) {
-                        const uint64_t w = ld_relaxed(m);
-                        if (w & TPL_X) {
-                            ok = false;
-                        } else if (w & TPL_S_MASK) {
-                            // blocked by readers only: hold off new readers
-                            if (!(w & TPL_PENDING)) or64(m, TPL_PENDING);
-                            ok = false;
-                        } else {
-                            ok = cas64(m, w, TPL_X | (uint64_t)(t + 1)) == w;
-                        }
-                    }
+                    if (ok) ok = cas64(m, 0ull, TPL_X | (uint64_t)(t + 1)) == 0ull;
                     if (ok) held |= 1ull << k; else fail = true;
                 }
                 if (!fail) __threadfence();
@@ -415,44 +404,44 @@ __device__ __forceinline__ uint32_t backoff_rounds(const ExecArgs& a, uint32_t t
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
-template <int SCHEME, class Work>
-__global__ void __launch_bounds__(1024) exec_kernel(const ExecArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    Lane L;
-    L.G = a.lanes;
-    L.lane = threadIdx.x & 31;
-    L.lig = L.lane & (L.G - 1);
-    L.gbase = L.lane & ~(L.G - 1);
-    L.gmask = (L.G == 32) ? 0xffffffffu : (((1u << L.G) - 1u) << L.gbase);
-    const uint32_t slots = blockDim.x / L.G;
-    const uint32_t slot = threadIdx.x / L.G;
-    const uint32_t M = a.max_ops;
-    Stage S;
-    uint64_t* w64 = reinterpret_cast<uint64_t*>(smem);
-    S.desc = w64 + (size_t)slot * M;
-    S.obs = w64 + (size_t)slots * M + (size_t)slot * M;
-    ulonglong2* w128 = reinterpret_cast<ulonglong2*>(w64 + 2 * (size_t)slots * M);
-    S.oldv = w128 + (size_t)slot * M;
-    S.newv = w128 + (size_t)slots * M + (size_t)slot * M;
-
-    constexpr bool DENSE = SCHEME == GCC_NO_WAIT_2PL || SCHEME == GCC_DET;
-    const uint64_t deadline = globaltimer() + a.deadline_ns;
+struct Counters {
     unsigned commits = 0, aborts = 0, timeouts = 0, invalid = 0, max_att = 0;
+};
+
+// Hands out transactions of one batch in id order.
+struct SingleFetch {
+    const ExecArgs* a;
+    __device__ __forceinline__ bool next(const Lane& L, uint32_t& t, const ExecArgs*& A) {
+        unsigned long long tt = 0;
+        if (L.lig == 0) tt = agg_ticket(&a->st->fetch);
+        tt = __shfl_sync(L.gmask, tt, L.gbase);
+        if (tt >= a->n_txns) return false;
+        t = (uint32_t)tt;
+        A = a;
+        return true;
+    }
+    __device__ __forceinline__ void done(const Lane&, const ExecArgs&, Counters&) {}
+};
+
+// The execution loop of one lane group: take a transaction, stage and check
+// it, attempt it round after round until it commits or gives up.
+template <int SCHEME, class Work, class Fetch>
+__device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, uint64_t deadline,
+                           Counters& c) {
+    constexpr bool DENSE = SCHEME == GCC_NO_WAIT_2PL || SCHEME == GCC_DET;
     bool finished = false, has = false;
     uint32_t t = 0, nops = 0, attempts = 0, wait = 0;
     uint64_t first = 0;
+    const ExecArgs* A = nullptr;
 
     for (;;) {
         // 1. groups without a transaction take the next one
         if (!has && !finished) {
-            unsigned long long tt = 0;
-            if (L.lig == 0) tt = agg_ticket(&a.st->fetch);
-            tt = __shfl_sync(L.gmask, tt, L.gbase);
-            if (tt >= a.n_txns) {
+            if (!F.next(L, t, A)) {
                 finished = true;
             } else {
-                t = (uint32_t)tt;
-                const gcc_txn tx = a.txns[t];  // broadcast load
+                const ExecArgs& a = *A;
+                const gcc_txn tx = a.txns[t];
                 nops = tx.n_ops;
                 first = tx.first_op;
                 bool bad = nops > M || !Work::valid_txn(a, tx) || first + nops > a.n_ops;
@@ -480,8 +469,9 @@ __global__ void __launch_bounds__(1024) exec_kernel(const ExecArgs a) {
                         a.results[t] = gcc_txn_result{GCC_TXN_INVALID, 0u, ~0ull};
                         if (!DENSE) a.order_key[t] = ~0ull;
                         atomicOr(&a.st->error, GCC_DEVERR_INVALID);
-                        ++invalid;
+                        ++c.invalid;
                     }
+                    F.done(L, a, c);
                 } else {
                     has = true;
                     attempts = 0;
@@ -496,6 +486,7 @@ __global__ void __launch_bounds__(1024) exec_kernel(const ExecArgs a) {
         const bool go = has && wait == 0;
         if (has && wait > 0) --wait;
         if (go) {
+            const ExecArgs& a = *A;
             ++attempts;
             unsigned long long order_key = 0;
             int outcome;
@@ -508,7 +499,7 @@ __global__ void __launch_bounds__(1024) exec_kernel(const ExecArgs a) {
             else
                 outcome = det_attempt<Work>(a, L, S, t, first, nops, order_key);
             if (outcome == ABORT) {
-                if (L.lig == 0) ++aborts;
+                if (L.lig == 0) ++c.aborts;
                 if (attempts >= a.max_attempts) {
                     if (L.lig == 0) atomicOr(&a.st->error, GCC_DEVERR_ATTEMPTS);
                     outcome = GIVE_UP;
@@ -527,44 +518,74 @@ __global__ void __launch_bounds__(1024) exec_kernel(const ExecArgs a) {
                     a.results[t] = gcc_txn_result{GCC_TXN_COMMITTED, attempts,
                                                   DENSE ? (uint64_t)order_key : ~0ull};
                     if (!DENSE) a.order_key[t] = order_key;
-                    ++commits;
+                    ++c.commits;
                 }
             } else if (outcome == GIVE_UP) {
-                if constexpr (SCHEME == GCC_NO_WAIT_2PL) {
-                    // drop any writer-pending marks this transaction may have set
-                    for (uint32_t j = L.lig; j < nops; j += L.G) {
-                        const uint32_t r = Work::rec(a, S.desc[j]);
-                        if (r != NO_CC && Work::writes(S.desc[j])) and64(a.meta + r, ~TPL_PENDING);
-                    }
-                }
                 if (L.lig == 0) {
                     a.results[t] = gcc_txn_result{GCC_TXN_TIMEOUT, attempts, ~0ull};
                     if (!DENSE) a.order_key[t] = ~0ull;
-                    ++timeouts;
+                    ++c.timeouts;
                 }
             }
             if (outcome != ABORT) {
-                if (L.lig == 0 && attempts > max_att) max_att = attempts;
+                if (L.lig == 0 && attempts > c.max_att) c.max_att = attempts;
                 has = false;
+                F.done(L, a, c);
             }
             __syncwarp(L.gmask);
         }
         // 3. a warp where nobody attempted this round sleeps one quantum
-        if (!__any_sync(0xffffffffu, go)) __nanosleep(a.backoff_base_ns ? a.backoff_base_ns : 32);
+        if (!__any_sync(0xffffffffu, go)) {
+            const uint32_t q = A ? A->backoff_base_ns : 0u;
+            __nanosleep(q ? q : 32);
+        }
     }
-    // one atomic per warp and counter
-    commits = __reduce_add_sync(0xffffffffu, commits);
-    aborts = __reduce_add_sync(0xffffffffu, aborts);
-    timeouts = __reduce_add_sync(0xffffffffu, timeouts);
-    invalid = __reduce_add_sync(0xffffffffu, invalid);
-    max_att = __reduce_max_sync(0xffffffffu, max_att);
+}
+
+// Lane-group geometry and shared-memory staging of one block.
+__device__ __forceinline__ void setup_lanes(uint32_t G, uint32_t M, Lane& L, Stage& S) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    L.G = G;
+    L.lane = threadIdx.x & 31;
+    L.lig = L.lane & (L.G - 1);
+    L.gbase = L.lane & ~(L.G - 1);
+    L.gmask = (L.G == 32) ? 0xffffffffu : (((1u << L.G) - 1u) << L.gbase);
+    const uint32_t slots = blockDim.x / L.G;
+    const uint32_t slot = threadIdx.x / L.G;
+    uint64_t* w64 = reinterpret_cast<uint64_t*>(smem);
+    S.desc = w64 + (size_t)slot * M;
+    S.obs = w64 + (size_t)slots * M + (size_t)slot * M;
+    ulonglong2* w128 = reinterpret_cast<ulonglong2*>(w64 + 2 * (size_t)slots * M);
+    S.oldv = w128 + (size_t)slot * M;
+    S.newv = w128 + (size_t)slots * M + (size_t)slot * M;
+}
+
+// Warp-reduced counters into a batch's state: one atomic per warp and field.
+__device__ __forceinline__ void flush_counters(BatchState* st, Counters& c) {
+    const unsigned commits = __reduce_add_sync(0xffffffffu, c.commits);
+    const unsigned aborts = __reduce_add_sync(0xffffffffu, c.aborts);
+    const unsigned timeouts = __reduce_add_sync(0xffffffffu, c.timeouts);
+    const unsigned invalid = __reduce_add_sync(0xffffffffu, c.invalid);
+    const unsigned max_att = __reduce_max_sync(0xffffffffu, c.max_att);
     if ((threadIdx.x & 31) == 0) {
-        if (commits) atomicAdd(&a.st->committed, (unsigned long long)commits);
-        if (aborts) atomicAdd(&a.st->aborts, (unsigned long long)aborts);
-        if (timeouts) atomicAdd(&a.st->timeouts, (unsigned long long)timeouts);
-        if (invalid) atomicAdd(&a.st->invalid, (unsigned long long)invalid);
-        if (max_att) atomicMax(&a.st->max_attempts, (unsigned long long)max_att);
+        if (commits) atomicAdd(&st->committed, (unsigned long long)commits);
+        if (aborts) atomicAdd(&st->aborts, (unsigned long long)aborts);
+        if (timeouts) atomicAdd(&st->timeouts, (unsigned long long)timeouts);
+        if (invalid) atomicAdd(&st->invalid, (unsigned long long)invalid);
+        if (max_att) atomicMax(&st->max_attempts, (unsigned long long)max_att);
     }
+}
+
+template <int SCHEME, class Work>
+__global__ void __launch_bounds__(1024) exec_kernel(const __grid_constant__ ExecArgs a) {
+    Lane L;
+    Stage S;
+    setup_lanes(a.lanes, a.max_ops, L, S);
+    const uint64_t deadline = globaltimer() + a.deadline_ns;
+    Counters c;
+    SingleFetch F{&a};
+    group_loop<SCHEME, Work>(F, L, S, a.max_ops, deadline, c);
+    flush_counters(a.st, c);
 }
 
 template <int SCHEME, class Work>
@@ -579,9 +600,9 @@ cudaError_t launch_exec(const ExecArgs& a, int grid, int block, size_t smem, cud
     return cudaGetLastError();
 }
 
-template <int SCHEME, class Work>
-int exec_occupancy(int block, size_t smem) {
-    auto k = exec_kernel<SCHEME, Work>;
+// Resident blocks per SM of a kernel for a launch shape (0 = cannot launch).
+template <class K>
+int occupancy_of(K k, int block, size_t smem) {
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
@@ -598,6 +619,11 @@ int exec_occupancy(int block, size_t smem) {
         return 0;
     }
     return n;
+}
+
+template <int SCHEME, class Work>
+int exec_occupancy(int block, size_t smem) {
+    return occupancy_of(exec_kernel<SCHEME, Work>, block, smem);
 }
 
 }  // namespace gcc

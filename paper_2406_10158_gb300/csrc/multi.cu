@@ -1,0 +1,476 @@
+// multi.cu -- the batched form: many independent key-value batches (each on
+// its own database) in one persistent-kernel launch, optionally replayed as a
+// CUDA graph.
+//
+// Lane groups take transactions from one counter over the concatenation of
+// all batches, so large and small batches share the GPU without a launch per
+// batch; each transaction runs against its own database exactly as in the
+// single-batch kernel.  OCC and TO draw timestamps from one clock shared by
+// the launch (started above every database's own clock and written back to
+// them afterwards), so commit ranks for all batches come from two sorts: by
+// timestamp, then stably by batch.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kv_work.cuh"
+#include "runtime.cuh"
+
+namespace gcc {
+namespace {
+
+constexpr uint32_t MAX_BATCHES = 256;
+
+struct MultiState {
+    unsigned long long fetch;
+    unsigned long long total;
+    DbState clock;                 // shared OCC / TO clock of the launch
+};
+
+__device__ __forceinline__ uint32_t find_batch(const uint32_t* prefix, uint32_t n, uint64_t g) {
+    uint32_t lo = 0, hi = n;       // prefix[lo] <= g < prefix[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (prefix[mid] <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+struct MultiFetch {
+    const ExecArgs* args;
+    const uint32_t* prefix;        // shared-memory copy, n + 1 entries
+    uint32_t n;
+    MultiState* ms;
+    Counters* c;
+    const ExecArgs* cur;
+
+    // Counters of the lane-group leader into the batch they belong to.
+    __device__ __forceinline__ void flush(const Lane& L) {
+        if (cur && L.lig == 0) {
+            BatchState* st = cur->st;
+            if (c->commits) atomicAdd(&st->committed, (unsigned long long)c->commits);
+            if (c->aborts) atomicAdd(&st->aborts, (unsigned long long)c->aborts);
+            if (c->timeouts) atomicAdd(&st->timeouts, (unsigned long long)c->timeouts);
+            if (c->invalid) atomicAdd(&st->invalid, (unsigned long long)c->invalid);
+            if (c->max_att) atomicMax(&st->max_attempts, (unsigned long long)c->max_att);
+        }
+        *c = Counters{};
+    }
+    __device__ __forceinline__ bool next(const Lane& L, uint32_t& t, const ExecArgs*& A) {
+        unsigned long long g = 0;
+        if (L.lig == 0) g = agg_ticket(&ms->fetch);
+        g = __shfl_sync(L.gmask, g, L.gbase);
+        if (g >= ms->total) return false;
+        const uint32_t i = find_batch(prefix, n, g);
+        A = args + i;
+        t = (uint32_t)(g - prefix[i]);
+        if (A != cur) {
+            flush(L);
+            cur = A;
+        }
+        return true;
+    }
+    __device__ __forceinline__ void done(const Lane&, const ExecArgs&, Counters&) {}
+};
+
+template <int SCHEME, class Work>
+__global__ void __launch_bounds__(1024)
+multi_kernel(const ExecArgs* __restrict__ args, const uint32_t* __restrict__ prefix, uint32_t n,
+             MultiState* ms, uint32_t lanes, uint32_t max_ops, uint64_t deadline_ns) {
+    __shared__ uint32_t prefix_s[MAX_BATCHES + 1];
+    for (uint32_t i = threadIdx.x; i <= n; i += blockDim.x) prefix_s[i] = prefix[i];
+    __syncthreads();
+    Lane L;
+    Stage S;
+    setup_lanes(lanes, max_ops, L, S);
+    const uint64_t deadline = globaltimer() + deadline_ns;
+    Counters c;
+    MultiFetch F{args, prefix_s, n, ms, &c, nullptr};
+    group_loop<SCHEME, Work>(F, L, S, max_ops, deadline, c);
+    F.flush(L);
+}
+
+// Per-batch states zeroed, the shared clock started above every database's.
+__global__ void multi_begin(const ExecArgs* __restrict__ args, DbState* const* __restrict__ own,
+                            uint32_t n, MultiState* ms, int scheme) {
+    __shared__ unsigned long long occ, to;
+    if (threadIdx.x == 0) {
+        occ = 0;
+        to = 0;
+        for (uint32_t i = 0; i < n; ++i) {
+            occ = max(occ, own[i]->occ_clock);
+            to = max(to, own[i]->to_clock);
+        }
+        ms->fetch = 0;
+        ms->clock.occ_clock = occ;
+        ms->clock.to_clock = to;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        BatchState z{};
+        z.ticket_base = scheme == GCC_TO ? to : occ;
+        *args[i].st = z;
+    }
+}
+
+// Every database continues its own clock from the shared one.
+__global__ void multi_end(DbState* const* __restrict__ own, uint32_t n, const MultiState* ms) {
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        own[i]->occ_clock = max(own[i]->occ_clock, ms->clock.occ_clock);
+        own[i]->to_clock = max(own[i]->to_clock, ms->clock.to_clock);
+    }
+}
+
+__global__ void multi_rank_keys(const ExecArgs* __restrict__ args, const uint32_t* __restrict__ prefix,
+                                uint32_t n, uint64_t total, uint32_t* __restrict__ keys,
+                                uint32_t* __restrict__ vals) {
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const uint32_t i = find_batch(prefix, n, g);
+    const ExecArgs& a = args[i];
+    const uint32_t t = (uint32_t)(g - prefix[i]);
+    const unsigned long long base = a.st->ticket_base;
+    keys[g] = a.results[t].status == GCC_TXN_COMMITTED ? (uint32_t)(a.order_key[t] - base)
+                                                       : 0xffffffffu;
+    vals[g] = (uint32_t)g;
+}
+
+// After sorting by timestamp: key each position by its batch for a stable
+// second sort that groups batches while keeping timestamp order inside.
+__global__ void multi_batch_keys(const uint32_t* __restrict__ prefix, uint32_t n, uint64_t total,
+                                 uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals) {
+    const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < total) keys[p] = find_batch(prefix, n, vals[p]);
+}
+
+__global__ void multi_ranks(const ExecArgs* __restrict__ args, const uint32_t* __restrict__ prefix,
+                            uint32_t n, uint64_t total, const uint32_t* __restrict__ vals) {
+    const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    const uint32_t g = vals[p];
+    const uint32_t i = find_batch(prefix, n, g);
+    const ExecArgs& a = args[i];
+    const uint32_t t = g - prefix[i];
+    if (a.results[t].status == GCC_TXN_COMMITTED) a.results[t].commit_order = p - prefix[i];
+}
+
+template <int SCHEME, int FB>
+int multi_occupancy(int block, size_t smem) {
+    return occupancy_of(multi_kernel<SCHEME, KvWork<FB>>, block, smem);
+}
+
+template <int SCHEME, int FB>
+cudaError_t multi_launch_kernel(const ExecArgs* args, const uint32_t* prefix, uint32_t n,
+                                MultiState* ms, uint32_t lanes, uint32_t max_ops,
+                                uint64_t deadline_ns, int grid, int block, size_t smem,
+                                cudaStream_t st) {
+    multi_kernel<SCHEME, KvWork<FB>><<<grid, block, smem, st>>>(args, prefix, n, ms, lanes, max_ops,
+                                                              deadline_ns);
+    return cudaGetLastError();
+}
+
+int occupancy_for(gcc_scheme scheme, uint32_t fb, int block, size_t smem) {
+    switch (scheme) {
+        case GCC_NO_WAIT_2PL:
+            return fb == 16 ? multi_occupancy<GCC_NO_WAIT_2PL, 16>(block, smem)
+                            : multi_occupancy<GCC_NO_WAIT_2PL, 8>(block, smem);
+        case GCC_TO:
+            return fb == 16 ? multi_occupancy<GCC_TO, 16>(block, smem)
+                            : multi_occupancy<GCC_TO, 8>(block, smem);
+        case GCC_OCC:
+            return fb == 16 ? multi_occupancy<GCC_OCC, 16>(block, smem)
+                            : multi_occupancy<GCC_OCC, 8>(block, smem);
+        default:
+            return 0;
+    }
+}
+
+inline unsigned blocks_for(uint64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+}  // namespace gcc
+
+using namespace gcc::rt;
+
+struct gcc_multi_plan {
+    gcc_scheme scheme = GCC_OCC;
+    int device = 0;
+    uint32_t n = 0;
+    uint32_t field_bytes = 8;
+    uint64_t total = 0;
+    gcc_exec_params p{};
+    std::vector<gcc_db*> dbs;
+    std::vector<uint32_t> h_prefix;
+    gcc::ExecArgs* d_args = nullptr;
+    uint32_t* d_prefix = nullptr;
+    gcc::DbState** d_own = nullptr;
+    gcc::MultiState* d_ms = nullptr;
+    gcc::SortScratch sort{};
+    int grid = 0, block = 0;
+    size_t smem = 0;
+    uint32_t max_ops = 0;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    uint32_t launches = 0;
+};
+
+namespace {
+
+void free_plan(gcc_multi_plan* pl) {
+    cudaSetDevice(pl->device);
+    if (pl->stream) cudaStreamSynchronize(pl->stream);
+    if (pl->graph) cudaGraphExecDestroy(pl->graph);
+    cudaFree(pl->d_args);
+    cudaFree(pl->d_prefix);
+    cudaFree(pl->d_own);
+    cudaFree(pl->d_ms);
+    cudaFree(pl->sort.k0);
+    cudaFree(pl->sort.v0);
+    cudaFree(pl->sort.k1);
+    cudaFree(pl->sort.v1);
+    cudaFree(pl->sort.hist);
+    cudaFree(pl->sort.totals);
+    if (pl->stream) cudaStreamDestroy(pl->stream);
+    delete pl;
+}
+
+MetaState state_after(gcc_scheme s) {
+    return s == GCC_OCC ? META_OCC : s == GCC_TO ? META_TO : META_ZERO;
+}
+
+// The launch sequence, all stream-ordered and allocation-free.
+gcc_status enqueue(gcc_multi_plan* pl, cudaStream_t st) {
+    using namespace gcc;
+    multi_begin<<<1, 256, 0, st>>>(pl->d_args, pl->d_own, pl->n, pl->d_ms, (int)pl->scheme);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        const uint32_t lanes = pl->p.lanes_per_txn;
+        const uint64_t dl = pl->p.deadline_ns;
+        switch (pl->scheme) {
+            case GCC_NO_WAIT_2PL:
+                e = pl->field_bytes == 16
+                        ? multi_launch_kernel<GCC_NO_WAIT_2PL, 16>(pl->d_args, pl->d_prefix, pl->n, pl->d_ms, lanes, pl->max_ops, dl, pl->grid, pl->block, pl->smem, st)
+                        : multi_launch_kernel<GCC_NO_WAIT_2PL, 8>(pl->d_args, pl->d_prefix, pl->n, pl->d_ms, lanes, pl->max_ops, dl, pl->grid, pl->block, pl->smem, st);
+                break;
+            case GCC_TO:
+                e = pl->field_bytes == 16
+                        ? multi_launch_kernel<GCC_TO, 16>(pl->d_args, pl->d_prefix, pl->n, pl->d_ms, lanes, pl->max_ops, dl, pl->grid, pl->block, pl->smem, st)
+                        : multi_launch_kernel<GCC_TO, 8>(pl->d_args, pl->d_prefix, pl->n, pl->d_ms, lanes, pl->max_ops, dl, pl->grid, pl->block, pl->smem, st);
+                break;
+            default:
+                e = pl->field_bytes == 16
+                        ? multi_launch_kernel<GCC_OCC, 16>(pl->d_args, pl->d_prefix, pl->n, pl->d_ms, lanes, pl->max_ops, dl, pl->grid, pl->block, pl->smem, st)
+                        : multi_launch_kernel<GCC_OCC, 8>(pl->d_args, pl->d_prefix, pl->n, pl->d_ms, lanes, pl->max_ops, dl, pl->grid, pl->block, pl->smem, st);
+                break;
+        }
+    }
+    uint32_t launches = 2;
+    if (e == cudaSuccess && pl->scheme != GCC_NO_WAIT_2PL && pl->total) {
+        multi_rank_keys<<<blocks_for(pl->total, 256), 256, 0, st>>>(pl->d_args, pl->d_prefix, pl->n,
+                                                                 pl->total, pl->sort.k0, pl->sort.v0);
+        uint32_t *sk, *sv;
+        e = radix_sort_pairs(pl->sort, pl->total, 32, &sk, &sv, st);   // by timestamp
+        if (e == cudaSuccess) {
+            multi_batch_keys<<<blocks_for(pl->total, 256), 256, 0, st>>>(pl->d_prefix, pl->n, pl->total,
+                                                                      sk, sv);
+            // the second sort reads from (k0, v0): four timestamp passes end there
+            e = radix_sort_pairs(pl->sort, pl->total, 8, &sk, &sv, st);  // stably by batch
+        }
+        if (e == cudaSuccess)
+            multi_ranks<<<blocks_for(pl->total, 256), 256, 0, st>>>(pl->d_args, pl->d_prefix, pl->n,
+                                                                 pl->total, sv);
+        launches += 1 + 12 + 1 + 3 + 1;
+    }
+    if (e == cudaSuccess) {
+        multi_end<<<1, 256, 0, st>>>(pl->d_own, pl->n, pl->d_ms);
+        e = cudaGetLastError();
+        launches += 1;
+    }
+    if (e != cudaSuccess) return fail(GCC_ERR_CUDA, "multi launch: %s", cudaGetErrorString(e));
+    pl->launches = launches;
+    return GCC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gcc_status gcc_multi_plan_create(gcc_scheme scheme, const gcc_multi_batch* b, uint32_t n,
+                                 const gcc_exec_params* params, gcc_multi_plan** out) {
+    if (!b || !out || n == 0) return fail(GCC_ERR_INVALID, "null argument or no batches");
+    *out = nullptr;
+    if (n > gcc::MAX_BATCHES) return fail(GCC_ERR_CAPACITY, "at most 256 batches per plan");
+    if (scheme != GCC_OCC && scheme != GCC_NO_WAIT_2PL && scheme != GCC_TO)
+        return fail(GCC_ERR_INVALID, "the batched form runs OCC, NO_WAIT 2PL or TO");
+    gcc_exec_params p = merged(params);
+    gcc_status s = validate_params(p);
+    if (s) return s;
+    const int dev = b[0].db ? b[0].db->d.device : 0;
+    uint32_t fb = b[0].db ? b[0].db->d.field_bytes : 8, max_ops = 0;
+    uint64_t total = 0;
+    std::vector<uint32_t> prefix(n + 1, 0);
+    for (uint32_t i = 0; i < n; ++i) {
+        gcc_db* db = b[i].db;
+        if (!db || db->d.schema != GCC_SCHEMA_KV)
+            return fail(GCC_ERR_INVALID, "batch %u: a key-value database is required", i);
+        if (db->d.device != dev || db->d.field_bytes != fb)
+            return fail(GCC_ERR_INVALID, "batch %u: all databases share one device and slot width", i);
+        for (uint32_t j = 0; j < i; ++j)
+            if (b[j].db == db) return fail(GCC_ERR_INVALID, "batch %u: database used twice", i);
+        if (b[i].n_txns > db->d.max_batch_txns || b[i].n_ops > db->d.max_batch_ops)
+            return fail(GCC_ERR_CAPACITY, "batch %u exceeds its database's maxima", i);
+        if ((b[i].n_txns && (!b[i].d_txns || !b[i].d_results)) ||
+            (b[i].n_ops && (!b[i].d_ops || !b[i].d_operands || !b[i].d_reads)))
+            return fail(GCC_ERR_INVALID, "batch %u: null pointer", i);
+        max_ops = std::max(max_ops, db->d.max_ops_per_txn);
+        total += b[i].n_txns;
+        prefix[i + 1] = (uint32_t)total;
+    }
+    if (total >= (1ull << 32)) return fail(GCC_ERR_CAPACITY, "more than 2^32 transactions");
+    if (cudaSetDevice(dev) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return fail(GCC_ERR_CUDA, "cannot select device %d", dev);
+
+    gcc_multi_plan* pl = new (std::nothrow) gcc_multi_plan();
+    if (!pl) return fail(GCC_ERR_NOMEM, "host allocation failed");
+    auto bail = [&](gcc_status st) { free_plan(pl); return st; };
+    pl->scheme = scheme;
+    pl->device = dev;
+    pl->n = n;
+    pl->field_bytes = fb;
+    pl->total = total;
+    pl->p = p;
+    pl->h_prefix = prefix;
+    pl->max_ops = max_ops;
+    if (cudaStreamCreateWithFlags(&pl->stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(GCC_ERR_CUDA, "cannot create stream"));
+    auto alloc = [&](void** ptr, size_t bytes) {
+        return cudaMalloc(ptr, bytes ? bytes : 1) == cudaSuccess;
+    };
+    const uint64_t items = std::max<uint64_t>(total, 1);
+    if (!alloc((void**)&pl->d_args, sizeof(gcc::ExecArgs) * n) ||
+        !alloc((void**)&pl->d_prefix, sizeof(uint32_t) * (n + 1)) ||
+        !alloc((void**)&pl->d_own, sizeof(gcc::DbState*) * n) ||
+        !alloc((void**)&pl->d_ms, sizeof(gcc::MultiState)) ||
+        !alloc((void**)&pl->sort.k0, items * 4) || !alloc((void**)&pl->sort.v0, items * 4) ||
+        !alloc((void**)&pl->sort.k1, items * 4) || !alloc((void**)&pl->sort.v1, items * 4) ||
+        !alloc((void**)&pl->sort.hist, gcc::sort_max_tiles(items) * 256 * 4) ||
+        !alloc((void**)&pl->sort.totals, 256 * 4))
+        return bail(fail(GCC_ERR_NOMEM, "cannot allocate the plan"));
+    pl->sort.max_items = items;
+
+    std::vector<gcc::ExecArgs> args(n);
+    std::vector<gcc::DbState*> own(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        gcc_db* db = b[i].db;
+        pl->dbs.push_back(db);
+        own[i] = db->dbs;
+        gcc::ExecArgs& a = args[i];
+        a = gcc::ExecArgs{};
+        a.txns = b[i].d_txns;
+        a.ops = reinterpret_cast<const uint64_t*>(b[i].d_ops);
+        a.operands = reinterpret_cast<const ulonglong2*>(b[i].d_operands);
+        a.n_txns = b[i].n_txns;
+        a.n_ops = b[i].n_ops;
+        a.results = b[i].d_results;
+        a.reads = reinterpret_cast<ulonglong2*>(b[i].d_reads);
+        a.table = db->table;
+        a.n_records = db->d.n_records;
+        a.n_fields = db->d.n_fields;
+        a.meta = db->meta;
+        a.n_meta = db->n_meta;
+        a.order_key = db->order_key;
+        a.order_key_uses_base = scheme != GCC_NO_WAIT_2PL;
+        a.st = db->st;
+        a.dbs = reinterpret_cast<gcc::DbState*>(reinterpret_cast<char*>(pl->d_ms) +
+                                                offsetof(gcc::MultiState, clock));
+        a.lanes = p.lanes_per_txn;
+        a.max_ops = max_ops;
+        a.collapse = p.collapse;
+        a.backoff_base_ns = p.immediate_restart ? 0u : p.backoff_base_ns;
+        a.backoff_cap_ns = p.backoff_cap_ns;
+        a.max_attempts = p.max_attempts;
+        a.read_retries = p.read_retries;
+        a.inject_ppm = p.inject_abort_ppm;
+        a.wait_budget_ns = p.wait_budget_ns;
+        a.deadline_ns = p.deadline_ns;
+        a.seed = p.seed ^ (0x9E3779B97F4A7C15ull * (i + 1));
+        // control words in a state this scheme can start from
+        if ((s = prepare_meta(db, scheme, pl->stream))) return bail(s);
+        db->meta_state = state_after(scheme);
+    }
+    gcc::MultiState ms{};
+    ms.total = total;
+    if (cudaMemcpy(pl->d_args, args.data(), sizeof(gcc::ExecArgs) * n, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(pl->d_prefix, prefix.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(pl->d_own, own.data(), sizeof(gcc::DbState*) * n, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(pl->d_ms, &ms, sizeof ms, cudaMemcpyHostToDevice) ||
+        cudaStreamSynchronize(pl->stream))
+        return bail(fail(GCC_ERR_CUDA, "cannot upload the plan"));
+
+    pl->block = (int)p.warps_per_block * 32;
+    const uint32_t slots = pl->block / p.lanes_per_txn;
+    pl->smem = (size_t)slots * max_ops * gcc::STAGE_BYTES_PER_OP;
+    const int occ = gcc::occupancy_for(scheme, fb, pl->block, pl->smem);
+    if (occ <= 0) return bail(fail(GCC_ERR_INVALID, "launch shape does not fit an SM"));
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = p.blocks_per_sm ? std::min<int>(p.blocks_per_sm, occ) : occ;
+    pl->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm,
+                                                           ((int64_t)total + slots - 1) / slots));
+    *out = pl;
+    return GCC_OK;
+}
+
+gcc_status gcc_multi_launch(gcc_multi_plan* pl, int use_graph, void* stream) {
+    if (!pl) return fail(GCC_ERR_INVALID, "null plan");
+    if (cudaSetDevice(pl->device) != cudaSuccess) return fail(GCC_ERR_CUDA, "cannot select device");
+    for (gcc_db* db : pl->dbs)
+        if (db->meta_state != META_ZERO && db->meta_state != state_after(pl->scheme))
+            return fail(GCC_ERR_INVALID, "a database ran another scheme since the plan was made");
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : pl->stream;
+    if (!use_graph) return enqueue(pl, st);
+    if (!pl->graph) {
+        // capture the whole launch sequence once on the plan's own stream
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(pl->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return fail(GCC_ERR_CUDA, "cannot begin stream capture");
+        gcc_status s = enqueue(pl, pl->stream);
+        const cudaError_t ec = cudaStreamEndCapture(pl->stream, &g);
+        if (s) { if (g) cudaGraphDestroy(g); return s; }
+        if (ec != cudaSuccess) return fail(GCC_ERR_CUDA, "capture failed: %s", cudaGetErrorString(ec));
+        const cudaError_t ei = cudaGraphInstantiate(&pl->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return fail(GCC_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(ei));
+    }
+    if (cudaGraphLaunch(pl->graph, st) != cudaSuccess) return fail(GCC_ERR_CUDA, "graph launch failed");
+    return GCC_OK;
+}
+
+gcc_status gcc_multi_stats(gcc_multi_plan* pl, uint32_t i, gcc_batch_stats* stats) {
+    if (!pl || !stats || i >= pl->n) return fail(GCC_ERR_INVALID, "bad plan, index or output");
+    if (cudaSetDevice(pl->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return fail(GCC_ERR_CUDA, "synchronisation failed");
+    gcc::BatchState h{};
+    if (cudaMemcpy(&h, pl->dbs[i]->st, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(GCC_ERR_CUDA, "cannot read batch state");
+    *stats = gcc_batch_stats{};
+    stats->n_txns = pl->h_prefix[i + 1] - pl->h_prefix[i];
+    stats->committed = h.committed;
+    stats->aborts = h.aborts;
+    stats->timeouts = h.timeouts;
+    stats->invalid = h.invalid;
+    stats->max_attempts = h.max_attempts;
+    stats->device_error = h.error;
+    stats->scheme = pl->scheme;
+    stats->kernel_launches = pl->launches;
+    stats->grid_blocks = (uint32_t)pl->grid;
+    return GCC_OK;
+}
+
+gcc_status gcc_multi_plan_destroy(gcc_multi_plan* pl) {
+    if (pl) free_plan(pl);
+    return GCC_OK;
+}
+
+}  // extern "C"

@@ -76,6 +76,39 @@ class StageTimes(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TuneSpace(ctypes.Structure):
+    _fields_ = [("n_lanes", ctypes.c_uint32), ("lanes", ctypes.c_uint32 * 6),
+                ("n_warps", ctypes.c_uint32), ("warps", ctypes.c_uint32 * 8),
+                ("n_caps", ctypes.c_uint32), ("caps", ctypes.c_uint32 * 4),
+                ("steps", ctypes.c_uint32), ("warmup", ctypes.c_uint32),
+                ("point_deadline_ns", ctypes.c_uint64)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_uint32), ("best_index", ctypes.c_uint32),
+                ("best_txn_per_s", ctypes.c_double), ("default_txn_per_s", ctypes.c_double)]
+
+
+def tune_space(lanes=(), warps=(), caps=(), steps=0, warmup=0, point_deadline_ns=0) -> TuneSpace:
+    sp = TuneSpace()
+    sp.n_lanes, sp.n_warps, sp.n_caps = len(lanes), len(warps), len(caps)
+    for i, v in enumerate(lanes):
+        sp.lanes[i] = v
+    for i, v in enumerate(warps):
+        sp.warps[i] = v
+    for i, v in enumerate(caps):
+        sp.caps[i] = v
+    sp.steps, sp.warmup, sp.point_deadline_ns = steps, warmup, point_deadline_ns
+    return sp
+
+
+class MultiBatch(ctypes.Structure):
+    _fields_ = [("db", ctypes.c_void_p), ("d_txns", ctypes.c_void_p), ("n_txns", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("d_ops", ctypes.c_void_p),
+                ("d_operands", ctypes.c_void_p), ("n_ops", ctypes.c_uint64),
+                ("d_results", ctypes.c_void_p), ("d_reads", ctypes.c_void_p)]
+
+
 class GCCError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -104,6 +137,14 @@ SIGNATURES = {
                                    ctypes.POINTER(ExecParams), P, P, P]),
     "gcc_last_stats": (ctypes.c_int, [P, ctypes.POINTER(BatchStats)]),
     "gcc_stage_history": (ctypes.c_int, [P, ctypes.c_uint32, P, ctypes.POINTER(ctypes.c_uint32)]),
+    "gcc_multi_plan_create": (ctypes.c_int, [ctypes.c_int, P, ctypes.c_uint32,
+                                             ctypes.POINTER(ExecParams), ctypes.POINTER(P)]),
+    "gcc_multi_launch": (ctypes.c_int, [P, ctypes.c_int, P]),
+    "gcc_multi_stats": (ctypes.c_int, [P, ctypes.c_uint32, ctypes.POINTER(BatchStats)]),
+    "gcc_multi_plan_destroy": (ctypes.c_int, [P]),
+    "gcc_autotune": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_uint32, P, P, ctypes.c_uint64,
+                                    P, P, ctypes.POINTER(TuneSpace), ctypes.POINTER(ExecParams),
+                                    ctypes.POINTER(TuneReport), P]),
     "gcc_det_execute_noalloc": (ctypes.c_int, [P, ctypes.c_uint32, ctypes.c_uint32,
                                                ctypes.c_uint32, P, ctypes.c_uint32, P, P,
                                                ctypes.c_uint32, ctypes.c_uint32, P, P, P]),
@@ -228,6 +269,42 @@ def gcc_stage_history(db: int, max_entries: int = 256) -> list:
     n = ctypes.c_uint32(0)
     _check(load().gcc_stage_history(db, max_entries, arr, ctypes.byref(n)))
     return [arr[i].as_dict() for i in range(n.value)]
+
+
+def gcc_autotune(db: int, scheme, txns_ptr: int, n_txns: int, ops_ptr: int, operands_ptr: int,
+                 n_ops: int, results_ptr: int, reads_ptr: int, space: Optional[TuneSpace] = None,
+                 stream: int = 0):
+    """Returns (best ExecParams, report dict)."""
+    best = ExecParams()
+    rep = TuneReport()
+    _check(load().gcc_autotune(db, _scheme(scheme), txns_ptr, n_txns, ops_ptr, operands_ptr,
+                               n_ops, results_ptr, reads_ptr,
+                               ctypes.byref(space) if space is not None else None,
+                               ctypes.byref(best), ctypes.byref(rep), stream or None))
+    return best, {k: getattr(rep, k) for k, _ in rep._fields_}
+
+
+def gcc_multi_plan_create(scheme, batches, p: Optional[ExecParams] = None) -> int:
+    arr = (MultiBatch * len(batches))(*batches)
+    h = P()
+    _check(load().gcc_multi_plan_create(_scheme(scheme), arr, len(batches),
+                                        ctypes.byref(p) if p is not None else None,
+                                        ctypes.byref(h)))
+    return h.value
+
+
+def gcc_multi_launch(plan: int, use_graph: bool = True, stream: int = 0):
+    _check(load().gcc_multi_launch(plan, int(use_graph), stream or None))
+
+
+def gcc_multi_stats(plan: int, i: int) -> dict:
+    st = BatchStats()
+    _check(load().gcc_multi_stats(plan, i, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def gcc_multi_plan_destroy(plan: int):
+    _check(load().gcc_multi_plan_destroy(plan))
 
 
 def gcc_last_error() -> str:
@@ -364,3 +441,36 @@ class Batch:
         if self.handle:
             gcc_batch_free(self.handle)
             self.handle = 0
+
+
+class MultiPlan:
+    """One persistent launch over several (database, device batch) pairs.
+
+    ``entries`` are (Database, d_txns, n_txns, d_ops, d_operands, n_ops,
+    d_results, d_reads) with torch CUDA tensors; the tensors must outlive the
+    plan."""
+
+    def __init__(self, scheme, entries, p: Optional[ExecParams] = None):
+        self._keep = entries
+        bs = [MultiBatch(db.handle, _tensor_ptr(tx), n_t, 0, _tensor_ptr(op), _tensor_ptr(od), n_o,
+                         _tensor_ptr(rs), _tensor_ptr(rd))
+              for (db, tx, n_t, op, od, n_o, rs, rd) in entries]
+        self.n = len(bs)
+        self.handle = gcc_multi_plan_create(scheme, bs, p)
+
+    def launch(self, use_graph: bool = True, stream: int = 0):
+        gcc_multi_launch(self.handle, use_graph, stream)
+
+    def stats(self, i: int) -> dict:
+        return gcc_multi_stats(self.handle, i)
+
+    def close(self):
+        if self.handle:
+            gcc_multi_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

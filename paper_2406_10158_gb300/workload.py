@@ -504,3 +504,27 @@ def order_entry(seed: int = SEEDS[2], W: int = 8, n_txns: int = 1 << 18, order_c
     batch = oe_batch(derive_seed(seed, 40 + W), W, n_txns)
     cap = order_cap or oe_order_cap([batch], W)
     return oe_initial_db(seed, W, cap), batch, cap
+
+
+# ---------------------------------------------------------------------------
+# batched form: many independent key-value databases
+# ---------------------------------------------------------------------------
+def batched_kv(seed: int = SEEDS[3], n_db: int = 64, rec_bits=(16, 22), txn_range=(1000, 262144),
+               ops_range=(4, 64), theta: float = 0.8, nfields: int = 8, read_ratio: float = 0.5):
+    """``n_db`` databases with 2^U(rec_bits) records (log-uniform sizes) of
+    ``nfields`` u64 fields (splitmix64 init), each with one batch whose size
+    is log-uniform in ``txn_range`` and whose transactions have a uniform
+    number of ops in ``ops_range`` over Zipf(theta) keys.
+    Returns a list of (n_records, table, batch)."""
+    rng = np.random.Generator(np.random.PCG64(derive_seed(seed, 51)))
+    out = []
+    for i in range(n_db):
+        bits = int(rng.integers(rec_bits[0], rec_bits[1] + 1))
+        nrec = 1 << bits
+        n_txns = int(round(math.exp(rng.uniform(math.log(txn_range[0]), math.log(txn_range[1])))))
+        s = derive_seed(seed, 1000 + i)
+        table = kv_table_splitmix(s, nrec, nfields)
+        batch = kv_batch(derive_seed(s, 3), nrec=nrec, nfields=nfields, n_txns=n_txns,
+                         ops_range=ops_range, read_ratio=read_ratio, theta=theta, field_bytes=8)
+        out.append((nrec, table, batch))
+    return out

@@ -15,6 +15,11 @@ pytestmark = pytest.mark.gpu
 SCHEMES = ["occ", "2pl", "to", "det", "det-dataflow"]
 
 
+# Under heavy contention no-wait locking and timestamp ordering need retry
+# windows of milliseconds (thousands of contenders x microseconds per hold).
+HOT = {"backoff_cap_ns": 16_000_000}
+
+
 def go(eng, db, scheme, batch, timeout_s=120, **kw):
     """Run a batch; "det-dataflow" is the deterministic scheme run op by op
     (key-value batches otherwise take the prefix-sum evaluation)."""
@@ -74,7 +79,7 @@ def test_lane_group_widths(eng, scheme, lanes):
         db.load_kv(table)
         # 1 lane per txn stages 32 txns x 40 ops per warp: keep the block small
         res, reads, stats = go(eng, db, scheme, batch, lanes_per_txn=lanes,
-                               warps_per_block=2 if lanes == 1 else 4)
+                               warps_per_block=2 if lanes == 1 else 4, **HOT)
         final = db.read_kv()
     assert stats["committed"] == batch.n_txns, stats
     check(table, final, batch, res, reads, scheme, stats)
@@ -90,7 +95,7 @@ def test_sixteen_byte_slots_contention(eng, scheme):
     with eng.Database("kv", n_records=nrec, n_fields=nf, field_bytes=16,
                       max_batch_txns=1 << 15) as db:
         db.load_kv(table)
-        res, reads, stats = go(eng, db, scheme, batch)
+        res, reads, stats = go(eng, db, scheme, batch, **HOT)
         final = db.read_kv()
     assert stats["committed"] == batch.n_txns, stats
     check(table, final, batch, res, reads, scheme, stats)
@@ -262,7 +267,7 @@ def test_hot_key_zipf_099(eng, scheme):
     batch = wl.kv_batch(13, nrec=nrec, nfields=2, n_txns=4096, read_ratio=0.5, theta=0.99)
     with eng.Database("kv", n_records=nrec, n_fields=2, field_bytes=8, max_batch_txns=4096) as db:
         db.load_kv(table)
-        res, reads, stats = go(eng, db, scheme, batch)
+        res, reads, stats = go(eng, db, scheme, batch, **HOT)
         final = db.read_kv()
     assert stats["committed"] == batch.n_txns, stats
     check(table, final, batch, res, reads, scheme, stats)
