@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(1024) exec_kernel(const __grid_constant__ Exec
 template <int SCHEME, class Work>
 cudaError_t launch_exec(const ExecArgs& a, int grid, int block, size_t smem, cudaStream_t s) {
     auto k = exec_kernel<SCHEME, Work>;
-    if (smem > 48 * 1024) {
+    if (smem > 40 * 1024) {
         const cudaError_t e =
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -607,8 +607,14 @@ int occupancy_of(K k, int block, size_t smem) {
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return 0;
-    if (smem > (size_t)optin) return 0;                  // the shape cannot launch at all
-    if (smem > 48 * 1024 &&
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (smem + fa.sharedSizeBytes > (size_t)optin) return 0;   // cannot launch at all
+    // raise the dynamic limit whenever static + dynamic passes the 48 KB default
+    if (smem + fa.sharedSizeBytes > 48 * 1024 &&
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();                              // leave no sticky error behind
         return 0;

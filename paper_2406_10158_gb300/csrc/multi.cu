@@ -165,6 +165,7 @@ cudaError_t multi_launch_kernel(const ExecArgs* args, const uint32_t* prefix, ui
                                 MultiState* ms, uint32_t lanes, uint32_t max_ops,
                                 uint64_t deadline_ns, int grid, int block, size_t smem,
                                 cudaStream_t st) {
+    // the dynamic shared-memory limit was raised when the plan measured occupancy
     multi_kernel<SCHEME, KvWork<FB>><<<grid, block, smem, st>>>(args, prefix, n, ms, lanes, max_ops,
                                                               deadline_ns);
     return cudaGetLastError();

@@ -85,9 +85,34 @@ def test_batched_form_guards_scheme_changes(eng):
     db, _, batch, *_ = dbs[0]
     db.run("2pl", batch)                  # leaves 2PL-compatible words: OCC may resume
     plan.launch(use_graph=True)
+    torch.cuda.synchronize()              # the plan's stream and the database's are separate
     db.run("to", batch)                   # 16-byte TO words: the plan must refuse
     with pytest.raises(eng.GCCError):
         plan.launch(use_graph=True)
     plan.close()
     for (d, *_rest) in dbs:
         d.close()
+
+
+def test_autotune_picks_a_valid_faster_point(eng):
+    import torch
+    nrec = 1 << 14
+    table = wl.kv_table_splitmix(4, nrec, 8)
+    batch = wl.kv_batch(5, nrec=nrec, nfields=8, n_txns=8192, theta=0.8)
+    with eng.Database("kv", n_records=nrec, n_fields=8, field_bytes=8, max_batch_txns=8192) as db:
+        db.load_kv(table)
+        tx, op, od = _dev(batch.txns), _dev(batch.ops), _dev(batch.operands)
+        res = torch.zeros(batch.n_txns * 16, dtype=torch.uint8, device="cuda")
+        reads = torch.zeros(batch.n_ops * 16, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        space = eng.tune_space(lanes=(4, 16), warps=(4, 8), caps=(65536, 1000000), steps=2)
+        best, rep = eng.gcc_autotune(db.handle, "occ", tx.data_ptr(), batch.n_txns, op.data_ptr(),
+                                     od.data_ptr(), batch.n_ops, res.data_ptr(), reads.data_ptr(),
+                                     space)
+        assert rep["points"] == 8
+        assert rep["best_txn_per_s"] >= rep["default_txn_per_s"] > 0
+        assert best.lanes_per_txn in (4, 16) or rep["best_txn_per_s"] == rep["default_txn_per_s"]
+        # the chosen parameters run a batch that replays exactly
+        state = db.read_kv()
+        r, rd, st = db.run("occ", batch, best)
+        assert oracle.replay_check(state, db.read_kv(), batch, r, rd)["ok"]
