@@ -339,6 +339,81 @@ gcc_status gcc_multi_stats(gcc_multi_plan *plan, uint32_t i, gcc_batch_stats *st
 /* Free the plan (waits for its stream).  NULL is a no-op. */
 gcc_status gcc_multi_plan_destroy(gcc_multi_plan *plan);
 
+/* Served form: a request loop that forms batches continuously.  Each lane
+ * serves one database: arriving transactions join the lane's forming batch
+ * until its transaction cap or its write-set budget (16 bytes per writing op)
+ * is reached, or until its oldest request has waited max_delay_ns; the batch
+ * is then copied to the device, executed and copied back on the lane's own
+ * streams while the next batch forms.  Up to `depth` batches per lane are in
+ * flight; lanes run concurrently.  Batches of one lane execute in formation
+ * order (batch_seq), so a lane's committed requests, in (batch_seq,
+ * commit_order) order, form one serial history of its database. */
+typedef struct gcc_server_lane {
+    gcc_db *db;
+    uint32_t scheme;             /* gcc_scheme */
+    uint32_t max_batch_txns;     /* <= the database's max_batch_txns */
+    uint64_t write_budget_bytes; /* per batch [16 * max_batch_txns * 16] */
+    uint64_t max_delay_ns;       /* [200000] */
+    uint32_t depth;              /* batches in flight, 1..8 [3] */
+    uint32_t reserved;           /* 0 */
+} gcc_server_lane;
+
+typedef struct gcc_completion {
+    uint64_t request;            /* id from gcc_server_enqueue / trace index */
+    uint32_t lane;
+    uint32_t status;             /* gcc_txn_status */
+    uint64_t batch_seq;          /* per lane, in execution order */
+    uint64_t commit_order;       /* within the batch */
+    uint64_t arrival_ns;         /* host steady clock */
+    uint64_t done_ns;            /* when the server saw the result on the host */
+} gcc_completion;
+
+typedef struct gcc_server gcc_server;
+
+/* Create a server over n_lanes lanes (distinct databases, one device).
+ * Allocates every slot's pinned host and device buffers up front. */
+gcc_status gcc_server_create(const gcc_server_lane *lanes, uint32_t n_lanes,
+                             const gcc_exec_params *params, gcc_server **out);
+
+/* Admit one transaction (host memory, copied) to `lane`.  Its ops start at
+ * ops[0] (txn->first_op is ignored).  arrival_ns is its arrival time on the
+ * host steady clock (see gcc_server_now_ns).  *request_id receives its id. */
+gcc_status gcc_server_enqueue(gcc_server *s, uint32_t lane, const gcc_txn *txn,
+                              const gcc_op *ops, const gcc_operand *operands,
+                              uint64_t arrival_ns, uint64_t *request_id);
+
+/* Launch batches that are full or past their delay, collect finished ones. */
+gcc_status gcc_server_pump(gcc_server *s);
+
+/* Launch every forming batch and wait for all of them. */
+gcc_status gcc_server_drain(gcc_server *s);
+
+/* Pop up to max completions (oldest first); read values of each completed
+ * request go to reads_out consecutively (may be NULL). */
+gcc_status gcc_server_completions(gcc_server *s, gcc_completion *out, gcc_operand *reads_out,
+                                  uint64_t reads_capacity, uint32_t max, uint32_t *n_out);
+
+/* Open-loop replay of a request trace: request i (ops at
+ * ops[txns[i].first_op ..]) arrives at start + arrival_offset_ns[i] for lane
+ * lane_of[i]; the loop admits arrivals, launches and collects batches until
+ * every request has completed.  out[i] and reads_out[txns[i].first_op ..]
+ * receive the outcome of request i. */
+gcc_status gcc_server_run_trace(gcc_server *s, uint32_t n, const uint32_t *lane_of,
+                                const gcc_txn *txns, const gcc_op *ops,
+                                const gcc_operand *operands, const uint64_t *arrival_offset_ns,
+                                gcc_completion *out, gcc_operand *reads_out);
+
+/* Host steady clock in nanoseconds (the clock of arrival_ns / done_ns). */
+uint64_t gcc_server_now_ns(void);
+
+/* Totals of a lane since creation: committed transactions, aborted
+ * attempts and batches completed. */
+gcc_status gcc_server_lane_totals(gcc_server *s, uint32_t lane, uint64_t *committed,
+                                  uint64_t *aborts, uint64_t *batches);
+
+/* Drain and free the server.  NULL is a no-op. */
+gcc_status gcc_server_destroy(gcc_server *s);
+
 /* Launch-parameter search space for gcc_autotune.  The paper finds that the
  * number of active lanes per warp and warps per block move throughput by up
  * to 10x (Sec. IV-C, Exp-3 to Exp-5); this searches the engine's equivalents

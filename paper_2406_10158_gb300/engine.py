@@ -109,6 +109,24 @@ class MultiBatch(ctypes.Structure):
                 ("d_results", ctypes.c_void_p), ("d_reads", ctypes.c_void_p)]
 
 
+class ServerLane(ctypes.Structure):
+    _fields_ = [("db", ctypes.c_void_p), ("scheme", ctypes.c_uint32),
+                ("max_batch_txns", ctypes.c_uint32), ("write_budget_bytes", ctypes.c_uint64),
+                ("max_delay_ns", ctypes.c_uint64), ("depth", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("request", ctypes.c_uint64), ("lane", ctypes.c_uint32), ("status", ctypes.c_uint32),
+                ("batch_seq", ctypes.c_uint64), ("commit_order", ctypes.c_uint64),
+                ("arrival_ns", ctypes.c_uint64), ("done_ns", ctypes.c_uint64)]
+
+
+COMPLETION_DTYPE = np.dtype([("request", "<u8"), ("lane", "<u4"), ("status", "<u4"),
+                             ("batch_seq", "<u8"), ("commit_order", "<u8"),
+                             ("arrival_ns", "<u8"), ("done_ns", "<u8")])
+
+
 class GCCError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -142,6 +160,20 @@ SIGNATURES = {
     "gcc_multi_launch": (ctypes.c_int, [P, ctypes.c_int, P]),
     "gcc_multi_stats": (ctypes.c_int, [P, ctypes.c_uint32, ctypes.POINTER(BatchStats)]),
     "gcc_multi_plan_destroy": (ctypes.c_int, [P]),
+    "gcc_server_create": (ctypes.c_int, [P, ctypes.c_uint32, ctypes.POINTER(ExecParams),
+                                         ctypes.POINTER(P)]),
+    "gcc_server_enqueue": (ctypes.c_int, [P, ctypes.c_uint32, P, P, P, ctypes.c_uint64,
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "gcc_server_pump": (ctypes.c_int, [P]),
+    "gcc_server_drain": (ctypes.c_int, [P]),
+    "gcc_server_completions": (ctypes.c_int, [P, P, P, ctypes.c_uint64, ctypes.c_uint32,
+                                              ctypes.POINTER(ctypes.c_uint32)]),
+    "gcc_server_run_trace": (ctypes.c_int, [P, ctypes.c_uint32, P, P, P, P, P, P, P]),
+    "gcc_server_now_ns": (ctypes.c_uint64, []),
+    "gcc_server_lane_totals": (ctypes.c_int, [P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                                              ctypes.POINTER(ctypes.c_uint64),
+                                              ctypes.POINTER(ctypes.c_uint64)]),
+    "gcc_server_destroy": (ctypes.c_int, [P]),
     "gcc_autotune": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_uint32, P, P, ctypes.c_uint64,
                                     P, P, ctypes.POINTER(TuneSpace), ctypes.POINTER(ExecParams),
                                     ctypes.POINTER(TuneReport), P]),
@@ -467,6 +499,79 @@ class MultiPlan:
     def close(self):
         if self.handle:
             gcc_multi_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop over one or more databases (lanes).
+
+    ``lanes`` are (Database, scheme, max_batch_txns, write_budget_bytes,
+    max_delay_ns, depth) tuples; zero budget/delay/depth take the defaults."""
+
+    def __init__(self, lanes, p: Optional[ExecParams] = None):
+        arr = (ServerLane * len(lanes))()
+        for i, (db, scheme, cap, budget, delay, depth) in enumerate(lanes):
+            arr[i] = ServerLane(db.handle, _scheme(scheme), cap, budget, delay, depth, 0)
+        self._dbs = [l[0] for l in lanes]
+        h = P()
+        _check(load().gcc_server_create(arr, len(lanes), ctypes.byref(p) if p is not None else None,
+                                        ctypes.byref(h)))
+        self.handle = h.value
+
+    @staticmethod
+    def now_ns() -> int:
+        return int(load().gcc_server_now_ns())
+
+    def enqueue(self, lane: int, txn: np.ndarray, ops: np.ndarray, operands: np.ndarray,
+                arrival_ns: int) -> int:
+        rid = ctypes.c_uint64(0)
+        _check(load().gcc_server_enqueue(self.handle, lane, _host_ptr(txn), _host_ptr(ops),
+                                         _host_ptr(operands), arrival_ns, ctypes.byref(rid)))
+        return rid.value
+
+    def pump(self):
+        _check(load().gcc_server_pump(self.handle))
+
+    def drain(self):
+        _check(load().gcc_server_drain(self.handle))
+
+    def completions(self, max_n: int = 1 << 16, reads_capacity: int = 1 << 20):
+        out = np.zeros(max_n, dtype=COMPLETION_DTYPE)
+        reads = np.zeros((reads_capacity, 2), dtype=np.uint64)
+        n = ctypes.c_uint32(0)
+        _check(load().gcc_server_completions(self.handle, _host_ptr(out), _host_ptr(reads),
+                                             reads_capacity, max_n, ctypes.byref(n)))
+        return out[: n.value], reads
+
+    def run_trace(self, lane_of: np.ndarray, batch: "wl.KVBatch", arrival_offset_ns: np.ndarray):
+        """Open-loop replay of a trace; returns (completions, reads[n_ops, 2])."""
+        n = batch.n_txns
+        out = np.zeros(n, dtype=COMPLETION_DTYPE)
+        reads = np.zeros((batch.n_ops, 2), dtype=np.uint64)
+        lane_of = np.ascontiguousarray(lane_of, dtype=np.uint32)
+        arr = np.ascontiguousarray(arrival_offset_ns, dtype=np.uint64)
+        _check(load().gcc_server_run_trace(self.handle, n, _host_ptr(lane_of),
+                                           _host_ptr(np.ascontiguousarray(batch.txns)),
+                                           _host_ptr(np.ascontiguousarray(batch.ops)),
+                                           _host_ptr(np.ascontiguousarray(batch.operands)),
+                                           _host_ptr(arr), _host_ptr(out), _host_ptr(reads)))
+        return out, reads
+
+    def lane_totals(self, lane: int) -> dict:
+        c, a, b = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(load().gcc_server_lane_totals(self.handle, lane, ctypes.byref(c), ctypes.byref(a),
+                                             ctypes.byref(b)))
+        return {"committed": c.value, "aborts": a.value, "batches": b.value}
+
+    def close(self):
+        if self.handle:
+            _check(load().gcc_server_destroy(self.handle))
             self.handle = 0
 
     def __del__(self):

@@ -528,3 +528,81 @@ def batched_kv(seed: int = SEEDS[3], n_db: int = 64, rec_bits=(16, 22), txn_rang
                          ops_range=ops_range, read_ratio=read_ratio, theta=theta, field_bytes=8)
         out.append((nrec, table, batch))
     return out
+
+
+# ---------------------------------------------------------------------------
+# served form: request traces
+# ---------------------------------------------------------------------------
+def poisson_arrivals(seed: int, n: int, rate_per_s: float) -> np.ndarray:
+    """Arrival offsets (ns, uint64) of an open-loop Poisson process."""
+    rng = np.random.Generator(np.random.PCG64(derive_seed(seed, 61)))
+    gaps = rng.exponential(1e9 / rate_per_s, size=n)
+    return np.cumsum(gaps).astype(np.uint64)
+
+
+def interleave(batches, lane_of: np.ndarray) -> KVBatch:
+    """One trace from per-lane batches: request i is the next transaction of
+    batches[lane_of[i]]; its ops are laid out contiguously in trace order."""
+    lane_of = np.asarray(lane_of)
+    n = lane_of.size
+    counts = [int(np.count_nonzero(lane_of == l)) for l in range(len(batches))]
+    for l, b in enumerate(batches):
+        if b.n_txns < counts[l]:
+            raise ValueError("lane %d has too few transactions" % l)
+    idx_in_lane = np.zeros(n, dtype=np.int64)
+    for l in range(len(batches)):
+        sel = lane_of == l
+        idx_in_lane[sel] = np.arange(counts[l])
+    txns = np.zeros(n, dtype=TXN_DTYPE)
+    src_first = np.zeros(n, dtype=np.int64)
+    nops = np.zeros(n, dtype=np.int64)
+    for l, b in enumerate(batches):
+        sel = lane_of == l
+        t = b.txns[idx_in_lane[sel]]
+        src_first[sel] = t["first_op"]
+        nops[sel] = t["n_ops"]
+        txns["type"][sel] = t["type"]
+    txns["n_ops"] = nops
+    first = np.zeros(n, dtype=np.int64)
+    if n:
+        first[1:] = np.cumsum(nops)[:-1]
+    txns["first_op"] = first
+    total = int(nops.sum())
+    ops = np.zeros(total, dtype=OP_DTYPE)
+    operands = np.zeros((total, 2), dtype=np.uint64)
+    rep = np.repeat(np.arange(n), nops)
+    within = np.arange(total) - np.repeat(first, nops)
+    src = np.repeat(src_first, nops) + within
+    for l, b in enumerate(batches):
+        sel = lane_of[rep] == l
+        ops[sel] = b.ops[src[sel]]
+        operands[sel] = b.operands[src[sel]]
+    return KVBatch(txns=txns, ops=ops, operands=operands)
+
+
+def select(batch: KVBatch, idx) -> KVBatch:
+    """The transactions ``idx`` of ``batch`` (in that order) as a batch of
+    their own."""
+    idx = np.asarray(idx, dtype=np.int64)
+    t = batch.txns[idx]
+    nops = t["n_ops"].astype(np.int64)
+    first = np.zeros(idx.size, dtype=np.int64)
+    if idx.size:
+        first[1:] = np.cumsum(nops)[:-1]
+    src = np.repeat(t["first_op"].astype(np.int64), nops) + \
+        (np.arange(int(nops.sum())) - np.repeat(first, nops))
+    txns = t.copy()
+    txns["first_op"] = first
+    return KVBatch(txns=txns, ops=batch.ops[src].copy(), operands=batch.operands[src].copy())
+
+
+def disjoint_kv(seed: int, n_txns: int, nrec: int, nfields: int, ops_per_txn: int = 16,
+                read_ratio: float = 0.8) -> KVBatch:
+    """Transactions on pairwise disjoint keys: request r uses keys
+    [r * ops_per_txn, (r + 1) * ops_per_txn)."""
+    if n_txns * ops_per_txn > nrec:
+        raise ValueError("not enough records for disjoint transactions")
+    b = kv_batch(seed, nrec=nrec, nfields=nfields, n_txns=n_txns, ops_per_txn=ops_per_txn,
+                 read_ratio=read_ratio, theta=0.0)
+    b.ops["key"] = np.arange(n_txns * ops_per_txn, dtype=np.uint32)
+    return b

@@ -1,0 +1,115 @@
+"""GPU parity of the served form (continuous batching over a request trace).
+
+A lane's committed requests, ordered by (batch_seq, commit_order), are one
+serial history of its database: the oracle replays that history from the
+initial state and must reproduce every read and the final state.  Requests on
+disjoint keys get bit-identical results alone and mixed with other traffic.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_10158_gb300 import workload as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_10158_gb300 import engine
+    return engine
+
+
+def lane_history(trace, lane_of, comp, reads, lane):
+    """(sub-batch in serial order, results with dense commit ranks, reads)."""
+    idx = np.nonzero(lane_of == lane)[0]
+    c = comp[idx]
+    assert (c["status"] == oracle.ST_COMMITTED).all()
+    order = np.lexsort((c["commit_order"], c["batch_seq"]))
+    sub = wl.select(trace, idx)
+    res = np.zeros(idx.size, dtype=wl.RESULT_DTYPE)
+    res["status"] = oracle.ST_COMMITTED
+    res["commit_order"][order] = np.arange(idx.size)
+    first = trace.txns["first_op"][idx].astype(np.int64)
+    nops = trace.txns["n_ops"][idx].astype(np.int64)
+    src = np.repeat(first, nops) + (np.arange(int(nops.sum())) -
+                                    np.repeat(np.concatenate([[0], np.cumsum(nops)[:-1]]), nops))
+    return sub, res, reads[src]
+
+
+@pytest.mark.parametrize("schemes", [("occ", "occ"), ("det", "2pl"), ("to", "det")])
+def test_served_mix_replays(eng, schemes):
+    nrec, W = 1 << 14, 2
+    table = wl.kv_table_splitmix(21, nrec, 8)
+    kv = wl.kv_batch(22, nrec=nrec, nfields=8, n_txns=4000, read_ratio=0.8, theta=0.8)
+    oe0, oe, cap = wl.order_entry(seed=23, W=W, n_txns=4000)
+    rng = np.random.default_rng(1)
+    lane_of = (rng.random(6000) < 0.5).astype(np.uint32)          # 0 = KV, 1 = order entry
+    trace = wl.interleave([kv, oe], lane_of)
+    arrivals = wl.poisson_arrivals(24, 6000, 2e6)
+    with eng.Database("kv", n_records=nrec, n_fields=8, field_bytes=8, max_batch_txns=512) as dkv, \
+            eng.Database("oe", n_warehouses=W, order_cap=cap, max_ops_per_txn=33,
+                         max_batch_txns=512, max_batch_ops=512 * 33) as doe:
+        dkv.load_kv(table)
+        doe.load_oe(oe0)
+        srv = eng.Server([(dkv, schemes[0], 512, 0, 50_000, 3), (doe, schemes[1], 512, 0, 50_000, 3)],
+                         eng.params(backoff_cap_ns=16_000_000))
+        comp, reads = srv.run_trace(lane_of, trace, arrivals)
+        tot = [srv.lane_totals(0), srv.lane_totals(1)]
+        srv.close()
+        final_kv, final_oe = dkv.read_kv(), doe.read_oe()
+    assert tot[0]["batches"] > 1 and tot[1]["batches"] > 1
+    assert (comp["done_ns"] >= comp["arrival_ns"]).all()
+    sub, res, rd = lane_history(trace, lane_of, comp, reads, 0)
+    rep = oracle.replay_check(table, final_kv, sub, res, rd)
+    assert rep["ok"], rep
+    sub, res, rd = lane_history(trace, lane_of, comp, reads, 1)
+    rep = oracle.oe_replay_check(oe0, final_oe, W, cap, sub, res, rd)
+    assert rep["ok"], rep
+    assert oracle.oe_consistency(final_oe, W, cap) == 0
+
+
+@pytest.mark.parametrize("scheme", ["occ", "det"])
+def test_served_same_alone_and_in_the_mix(eng, scheme):
+    """Requests on disjoint keys: identical reads and final table whether they
+    are served alone or interleaved with order-entry traffic (tolerance 0)."""
+    nrec, W = 1 << 16, 1
+    table = wl.kv_table_splitmix(31, nrec, 4)
+    kv = wl.disjoint_kv(32, 2000, nrec, 4)
+    oe0, oe, cap = wl.order_entry(seed=33, W=W, n_txns=3000)
+    outcomes = []
+    for mixed in (False, True):
+        if mixed:
+            lane_of = np.zeros(5000, dtype=np.uint32)
+            lane_of[np.random.default_rng(2).permutation(5000)[:3000]] = 1
+        else:
+            lane_of = np.zeros(2000, dtype=np.uint32)
+        trace = wl.interleave([kv, oe], lane_of)
+        arrivals = wl.poisson_arrivals(34, lane_of.size, 1e6)
+        with eng.Database("kv", n_records=nrec, n_fields=4, field_bytes=8, max_batch_txns=256) as dkv, \
+                eng.Database("oe", n_warehouses=W, order_cap=cap, max_ops_per_txn=33,
+                             max_batch_txns=256, max_batch_ops=256 * 33) as doe:
+            dkv.load_kv(table)
+            doe.load_oe(oe0)
+            srv = eng.Server([(dkv, scheme, 256, 0, 30_000, 2), (doe, "occ", 256, 0, 30_000, 2)])
+            comp, reads = srv.run_trace(lane_of, trace, arrivals)
+            srv.close()
+            final = dkv.read_kv()
+        kv_idx = np.nonzero(lane_of == 0)[0]
+        assert (comp["status"][kv_idx] == oracle.ST_COMMITTED).all()
+        sub = wl.select(trace, kv_idx)
+        first = trace.txns["first_op"][kv_idx].astype(np.int64)
+        kv_reads = np.concatenate([reads[f:f + 16] for f in first])
+        outcomes.append((kv_reads, final, sub))
+    (r0, f0, s0), (r1, f1, s1) = outcomes
+    assert np.array_equal(s0.ops, s1.ops)
+    assert np.array_equal(r0, r1)
+    assert np.array_equal(f0, f1)
+    # and both equal the serial execution of the requests
+    ref_final, ref_reads = oracle.serial(table, s0)
+    assert np.array_equal(ref_final, f0) and np.array_equal(ref_reads, r0)

@@ -1,0 +1,69 @@
+"""The seeded input generators (CPU only): shapes, ranges and distributions."""
+import numpy as np
+
+from paper_2406_10158_gb300 import workload as wl
+
+
+def test_feistel_is_a_bijection():
+    for n in (1 << 10, 1000, 65536):
+        p = wl.feistel_permute(np.arange(n, dtype=np.uint64), n, 7)
+        assert np.array_equal(np.sort(p), np.arange(n, dtype=np.uint64))
+
+
+def test_keys_distinct_within_each_transaction():
+    b = wl.kv_batch(3, nrec=64, nfields=2, n_txns=500, ops_per_txn=16, theta=0.99)
+    k = b.ops["key"].reshape(500, 16)
+    s = np.sort(k, axis=1)
+    assert not (s[:, 1:] == s[:, :-1]).any()
+    assert (k < 64).all()
+
+
+def test_zipf_head_frequency_matches_closed_form():
+    """Rank 0 of Zipf(theta) over N items has probability 1 / zeta(N, theta)."""
+    rng = np.random.default_rng(0)
+    n, theta, draws = 1 << 16, 0.8, 400_000
+    r = wl.zipf_ranks(rng, n, theta, draws)
+    zeta = np.sum(np.arange(1, n + 1, dtype=np.float64) ** -theta)
+    p0 = 1.0 / zeta
+    got = np.count_nonzero(r == 0) / draws
+    assert abs(got - p0) < 5 * np.sqrt(p0 / draws)
+    assert r.max() < n
+    u = wl.zipf_ranks(rng, n, 0.0, draws)           # theta 0 = uniform
+    assert abs(np.mean(u) / (n - 1) - 0.5) < 0.01
+
+
+def test_nurand_range_and_read_ratio():
+    rng = np.random.default_rng(1)
+    x = wl.nurand(rng, 8191, 1, 100000, 123, 100000)
+    assert x.min() >= 1 and x.max() <= 100000
+    b = wl.kv_batch(4, nrec=4096, nfields=8, n_txns=4000, read_ratio=0.8)
+    frac = np.mean(b.ops["kind"] == wl.OP_READ)
+    assert abs(frac - 0.8) < 0.01
+    assert not b.operands[b.ops["kind"] == wl.OP_READ].any()
+
+
+def test_order_entry_shapes():
+    db, b, cap = wl.order_entry(seed=5, W=2, n_txns=2000)
+    t = b.txns
+    no = t["type"] == wl.TXN_NEW_ORDER
+    assert ((t["n_ops"][no] >= 5) & (t["n_ops"][no] <= 33)).all()
+    assert (t["n_ops"][~no] == 3).all()
+    assert abs(no.mean() - 0.5) < 0.05
+    assert cap >= 3000
+
+
+def test_trace_interleave_and_select_round_trip():
+    kv = wl.kv_batch(1, nrec=1000, nfields=2, n_txns=50, ops_per_txn=3)
+    _, oe, _ = wl.order_entry(seed=2, W=1, n_txns=40)
+    lane_of = np.array([0] * 30 + [1] * 40 + [0] * 20, dtype=np.uint32)
+    np.random.default_rng(0).shuffle(lane_of)
+    tr = wl.interleave([kv, oe], lane_of)
+    assert tr.n_txns == 90
+    s0 = wl.select(tr, np.nonzero(lane_of == 0)[0])
+    s1 = wl.select(tr, np.nonzero(lane_of == 1)[0])
+    k, o = wl.select(kv, np.arange(50)), wl.select(oe, np.arange(40))
+    assert np.array_equal(s0.ops, k.ops) and np.array_equal(s0.operands, k.operands)
+    assert np.array_equal(s1.ops, o.ops) and np.array_equal(s1.txns, o.txns)
+    a = wl.poisson_arrivals(3, 10000, 1e6)
+    assert (np.diff(a.astype(np.int64)) >= 0).all()
+    assert abs(float(a[-1]) / 1e4 - 1000.0) < 50.0          # mean gap 1 us
