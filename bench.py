@@ -52,6 +52,13 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--seed", type=int, default=0x5EED0002)
+    p.add_argument("--form", choices=["plain", "batched", "served"], default="plain",
+                   help="plain: one batch per launch (the default line); batched: 64 "
+                        "databases in one persistent launch vs 64 plain launches; served: "
+                        "continuous batching of a Poisson trace vs plain per-batch launches")
+    p.add_argument("--n-db", type=int, default=64)
+    p.add_argument("--rates", default="1e5,1e6,1e7,1e8")
+    p.add_argument("--requests", type=int, default=1 << 18)
     return p.parse_args(argv)
 
 
@@ -350,6 +357,181 @@ def run_ours(args, rank, world, dist):
     return out
 
 
+# ---------------------------------------------------------------------------
+# batched form: 64 databases in one persistent launch
+# ---------------------------------------------------------------------------
+def run_batched(args, rank, world):
+    """64 key-value databases of 2^16..2^22 records (log-uniform), batches of
+    1,000..262,144 txns of 4..64 ops, Zipf 0.8, OCC: one graph-replayed
+    persistent launch against 64 plain launches on one stream, with launch
+    parameters from the autotuner (tuned on the median batch)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_10158_gb300 import engine as eng
+    from paper_2406_10158_gb300 import workload as wl
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    t0 = time.time()
+    spec = wl.batched_kv(wl.SEEDS[3] + rank, n_db=args.n_db)
+    gen_s = time.time() - t0
+    dbs, entries = [], []
+    up = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.uint8).reshape(-1)).to(dev)
+    for (nrec, table, batch) in spec:
+        db = eng.Database("kv", n_records=nrec, n_fields=8, field_bytes=8, max_ops_per_txn=64,
+                          max_batch_txns=batch.n_txns, max_batch_ops=batch.n_ops, device=dev)
+        db.load_kv(table)
+        e = (db, up(batch.txns), batch.n_txns, up(batch.ops), up(batch.operands), batch.n_ops,
+             torch.empty(batch.n_txns * 16, dtype=torch.uint8, device=dev),
+             torch.empty(batch.n_ops * 16, dtype=torch.uint8, device=dev))
+        dbs.append(db)
+        entries.append(e)
+    torch.cuda.synchronize(dev)
+    total_txns = sum(b.n_txns for (_, _, b) in spec)
+    # autotune on the median-size batch
+    order = sorted(range(len(spec)), key=lambda i: spec[i][2].n_txns)
+    m = order[len(order) // 2]
+    db, tx, n_t, op, od, n_o, rs, rd = entries[m]
+    space = eng.tune_space(lanes=(4, 8, 16, 32), warps=(4, 8, 16), caps=(65536, 1000000, 16000000),
+                           steps=2, warmup=1)
+    best, rep = eng.gcc_autotune(db.handle, "occ", tx.data_ptr(), n_t, op.data_ptr(), od.data_ptr(),
+                                 n_o, rs.data_ptr(), rd.data_ptr(), space)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / 1000.0
+
+    def plain():
+        for (db, tx, n_t, op, od, n_o, rs, rd) in entries:
+            db.execute("occ", tx, op, od, n_t, n_o, rs, rd, best, sh)
+
+    plan = eng.MultiPlan("occ", entries, best)
+    plan.launch(use_graph=True, stream=sh)            # capture once
+    torch.cuda.synchronize(dev)
+    steps = max(1, min(args.steps, 5))
+    with ClockSampler(dev) as clocks:
+        t_plain = timed(plain, steps)
+        committed_plain = sum(d.last_stats()["committed"] for d in dbs)
+        t_multi = timed(lambda: plan.launch(use_graph=True, stream=sh), steps)
+        committed_multi = sum(plan.stats(i)["committed"] for i in range(len(entries)))
+    plan.close()
+    for d in dbs:
+        d.close()
+    v_plain = committed_plain * steps / t_plain
+    v_multi = committed_multi * steps / t_multi
+    return {"metric": METRIC, "form": "batched", "value": v_multi, "unit": "txn/s", "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1000 * t_multi / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"{len(spec)} kv databases 2^16..2^22 x 8 u64, batches "
+                                   f"1000..262144 txns x 4..64 ops, zipf 0.8, occ",
+                       "total_txns": total_txns, "generation_s": round(gen_s, 1)},
+            "plain_launches": {"value": v_plain, "unit": "txn/s",
+                               "ms_per_step": 1000 * t_plain / steps},
+            "speedup_vs_plain": v_multi / v_plain,
+            "autotuned": {"lanes_per_txn": best.lanes_per_txn, "warps_per_block": best.warps_per_block,
+                          "backoff_cap_ns": best.backoff_cap_ns, "report": rep},
+            "all_committed": committed_multi == total_txns and committed_plain == total_txns,
+            "clocks": clocks.summary()}
+
+
+# ---------------------------------------------------------------------------
+# served form: continuous batching of a Poisson trace
+# ---------------------------------------------------------------------------
+def run_served(args, rank, world):
+    """Open-loop Poisson arrivals, 50/50 by count of key-value txns (2^24 x 8
+    u64, 16 ops, Zipf 0.8, 80% reads; deterministic scheme) and order-entry
+    txns (W = 8; OCC), at each offered rate: committed txns/s and p50/p99
+    latency (arrival to result on the host), against plain per-batch launches
+    of the same requests (submit, wait, next)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_10158_gb300 import engine as eng
+    from paper_2406_10158_gb300 import workload as wl
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    n = args.requests
+    nrec = 1 << 24
+    table = wl.kv_table_splitmix(wl.SEEDS[4], nrec, 8)
+    kv = wl.kv_batch(wl.derive_seed(wl.SEEDS[4], 1), nrec=nrec, nfields=8, n_txns=n,
+                     read_ratio=0.8, theta=0.8)
+    oe0, oe, cap = wl.order_entry(seed=wl.SEEDS[4], W=8, n_txns=n)   # every rate reloads it
+    rng = np.random.default_rng(7)
+    lane_of = (rng.random(n) < 0.5).astype(np.uint32)
+    trace = wl.interleave([kv, oe], lane_of)
+    max_batch = 1 << 14
+    lanes_kv = ("det", max_batch)
+    results = []
+    rates = [float(r) for r in args.rates.split(",")]
+
+    def fresh():
+        dkv = eng.Database("kv", n_records=nrec, n_fields=8, field_bytes=8,
+                           max_batch_txns=max_batch, device=dev)
+        doe = eng.Database("oe", n_warehouses=8, order_cap=cap, max_ops_per_txn=33,
+                           max_batch_txns=max_batch, max_batch_ops=max_batch * 33, device=dev)
+        dkv.load_kv(table)
+        doe.load_oe(oe0)
+        return dkv, doe
+
+    with ClockSampler(dev) as clocks:
+        for rate in rates:
+            arrivals = wl.poisson_arrivals(wl.SEEDS[4] + int(rate), n, rate)
+            dkv, doe = fresh()
+            srv = eng.Server([(dkv, lanes_kv[0], max_batch, 0, 100_000, 4),
+                              (doe, "occ", max_batch, 0, 100_000, 4)])
+            comp, _ = srv.run_trace(lane_of, trace, arrivals)
+            tots = [srv.lane_totals(0), srv.lane_totals(1)]
+            srv.close()
+            dkv.close()
+            doe.close()
+            ok = comp["status"] == 1
+            lat = (comp["done_ns"] - comp["arrival_ns"]).astype(np.float64) / 1e3
+            span = (comp["done_ns"].max() - comp["arrival_ns"].min()) / 1e9
+            results.append({"offered_txn_per_s": rate, "committed_txn_per_s": float(ok.sum() / span),
+                            "p50_latency_us": float(np.percentile(lat, 50)),
+                            "p99_latency_us": float(np.percentile(lat, 99)),
+                            "abort_rate": sum(t["aborts"] for t in tots) / max(1, sum(t["committed"] for t in tots)),
+                            "batches": sum(t["batches"] for t in tots),
+                            "all_committed": bool(ok.all())})
+        # plain per-batch launches of the same requests: submit, wait, next
+        dkv, doe = fresh()
+        subs = [wl.select(trace, np.nonzero(lane_of == l)[0]) for l in (0, 1)]
+        t0 = time.perf_counter()
+        committed = 0
+        for start in range(0, max(s.n_txns for s in subs), max_batch):
+            for l, (db, scheme) in enumerate(((dkv, lanes_kv[0]), (doe, "occ"))):
+                idx = np.arange(start, min(start + max_batch, subs[l].n_txns))
+                if idx.size:
+                    _, _, st = db.run(scheme, wl.select(subs[l], idx))
+                    committed += st["committed"]
+        plain_s = time.perf_counter() - t0
+        dkv.close()
+        doe.close()
+    best = max(results, key=lambda r: r["committed_txn_per_s"])
+    return {"metric": METRIC, "form": "served", "value": best["committed_txn_per_s"],
+            "unit": "txn/s", "n_gpus": world, "steps": len(rates), "warmup": 0,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"{n} requests, 50/50 kv (2^24 x 8 u64, 16 ops, zipf 0.8, 80% "
+                                   f"reads, det) and order-entry (W=8, occ), poisson arrivals",
+                       "max_batch_txns": max_batch, "max_delay_us": 100, "depth": 4},
+            "p99_latency_us": best["p99_latency_us"], "rates": results,
+            "plain_per_batch": {"value": committed / plain_s, "unit": "txn/s"},
+            "speedup_vs_plain": best["committed_txn_per_s"] / (committed / plain_s),
+            "clocks": clocks.summary()}
+
+
 def main(argv=None):
     args = parse_args(argv)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -366,6 +548,10 @@ def main(argv=None):
         dist = dist_mod
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.form == "batched":
+        out = run_batched(args, rank, world)
+    elif args.form == "served":
+        out = run_served(args, rank, world)
     else:
         out = run_ours(args, rank, world, dist)
     if out is not None and rank == 0:
