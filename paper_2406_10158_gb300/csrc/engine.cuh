@@ -126,13 +126,15 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // One ticket from a counter per calling lane, with one atomic per warp:
 // the lanes active at the call share a single atomicAdd.
-__device__ __forceinline__ unsigned long long agg_ticket(unsigned long long* ctr) {
+__device__ __forceinline__ unsigned long long agg_ticket(unsigned long long* ctr,
+                                                        unsigned step = 1) {
     unsigned mask = __activemask();
     int leader = __ffs(mask) - 1;
     unsigned long long base = 0;
-    if ((threadIdx.x & 31) == leader) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+    if ((threadIdx.x & 31) == leader)
+        base = atomicAdd(ctr, (unsigned long long)__popc(mask) * step);
     base = __shfl_sync(mask, base, leader);
-    return base + __popc(mask & lanemask_lt());
+    return base + (unsigned long long)__popc(mask & lanemask_lt()) * step;
 }
 
 // 64-bit mixing (splitmix64 finaliser) for jitter and abort injection.

@@ -106,20 +106,25 @@ __device__ int occ_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
                 S.oldv[j] = Work::load(a, d);
             } else {
                 uint64_t* m = a.meta + r;
+                // An unlocked version read with acquire, then the value.  The
+                // pair is checked later, not here: write keys by the lock CAS
+                // (it fails if the version moved), read keys by validation
+                // after the commit timestamp.  OCC writers install values only
+                // right before publishing a new version, so an unchanged
+                // unlocked version proves the value read belongs to it.
+                const bool w = Work::writes(d);
+                const ulonglong2 opd = w ? a.operands[first + j] : make_ulonglong2(0ull, 0ull);
                 for (uint32_t tries = 0;; ++tries) {
                     const uint64_t v1 = ld_acquire(m);
                     if (!(v1 & OCC_LOCK)) {
                         const ulonglong2 v = Work::load(a, d);
-                        __threadfence();
-                        if (ld_relaxed(m) == v1) {
-                            S.obs[j] = v1;
-                            S.oldv[j] = v;
-                            if (Work::writes(d))
-                                S.newv[j] = Work::compute(a, d, v, a.operands[first + j]);
-                            break;
-                        }
+                        S.obs[j] = v1;
+                        S.oldv[j] = v;
+                        if (w) S.newv[j] = Work::compute(a, d, v, opd);
+                        break;
                     }
                     if (tries >= a.read_retries) { fail = true; break; }
+                    __nanosleep(32);
                 }
             }
         }
@@ -264,9 +269,10 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
                 for (uint32_t tries = 0;; ++tries) {
                     const uint64_t y1 = ld_acquire(wts_word);
                     if ((y1 & TO_DIRTY) || ts < y1) { fail = true; break; }
+                    // raising RTS early only turns away older writers sooner, so
+                    // it goes out together with the value load
+                    max64(rts_word, ts);
                     const ulonglong2 v = Work::load(a, d);
-                    __threadfence();
-                    if (ld_relaxed(rts_word) < ts) max64(rts_word, ts);
                     __threadfence();
                     if (ld_relaxed(wts_word) == y1) { S.oldv[j] = v; break; }
                     if (tries >= a.read_retries) { fail = true; break; }
@@ -409,14 +415,25 @@ struct Counters {
 };
 
 // Hands out transactions of one batch in id order.
+// Transactions are handed out in chunks of CHUNK consecutive ids per lane
+// group: one atomic per warp and chunk on the shared counter instead of one
+// per transaction.  The deterministic scheme's waits need every fetched
+// transaction to be running (a group must never hold an unstarted id that
+// another group waits on while the warp's round waits for that group), so it
+// fetches one id at a time.
+template <unsigned CHUNK>
 struct SingleFetch {
     const ExecArgs* a;
+    unsigned long long next_id = 0, end_id = 0;
     __device__ __forceinline__ bool next(const Lane& L, uint32_t& t, const ExecArgs*& A) {
-        unsigned long long tt = 0;
-        if (L.lig == 0) tt = agg_ticket(&a->st->fetch);
-        tt = __shfl_sync(L.gmask, tt, L.gbase);
-        if (tt >= a->n_txns) return false;
-        t = (uint32_t)tt;
+        if (next_id >= end_id) {
+            unsigned long long tt = 0;
+            if (L.lig == 0) tt = agg_ticket(&a->st->fetch, CHUNK);
+            next_id = __shfl_sync(L.gmask, tt, L.gbase);
+            end_id = next_id + CHUNK;
+        }
+        if (next_id >= a->n_txns) return false;
+        t = (uint32_t)next_id++;
         A = a;
         return true;
     }
@@ -583,7 +600,7 @@ __global__ void __launch_bounds__(1024) exec_kernel(const __grid_constant__ Exec
     setup_lanes(a.lanes, a.max_ops, L, S);
     const uint64_t deadline = globaltimer() + a.deadline_ns;
     Counters c;
-    SingleFetch F{&a};
+    SingleFetch<SCHEME == GCC_DET ? 1u : 4u> F{&a};
     group_loop<SCHEME, Work>(F, L, S, a.max_ops, deadline, c);
     flush_counters(a.st, c);
 }
