@@ -113,6 +113,13 @@ __device__ __forceinline__ uint64_t or64(uint64_t* p, uint64_t v) {
 __device__ __forceinline__ uint64_t add64(uint64_t* p, uint64_t v) {
     return atomicAdd(reinterpret_cast<unsigned long long*>(p), v);
 }
+// Release/acquire fence at gpu scope.  Every ordering the schemes rely on is
+// release/acquire through an atomic on a shared location (a lock CAS, the
+// commit clock, a done counter), which this fence provides without the cost
+// of a sequentially consistent one.
+__device__ __forceinline__ void fence_acq_rel() {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

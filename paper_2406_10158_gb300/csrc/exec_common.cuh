@@ -144,7 +144,7 @@ __device__ int occ_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
     }
     fail = __any_sync(L.gmask, fail) || injected_abort(a, t, attempt);
     if (!fail) {
-        __threadfence();
+        fence_acq_rel();
         const unsigned long long ts = group_ticket(L, &a.dbs->occ_clock);
         // validate the read set against the versions observed
         for (uint32_t k = 0; k < kmax; ++k) {
@@ -161,7 +161,7 @@ __device__ int occ_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
                     const uint32_t j = L.lig + k * L.G;
                     Work::store(a, S.desc[j], S.newv[j], first + j);
                 }
-            __threadfence();
+            fence_acq_rel();
             for (uint32_t k = 0; k < kmax; ++k)
                 if (held >> k & 1)
                     st_relaxed(a.meta + Work::rec(a, S.desc[L.lig + k * L.G]), ts + 1);
@@ -206,7 +206,7 @@ __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
                     if (ok) ok = cas64(m, 0ull, TPL_X | (uint64_t)(t + 1)) == 0ull;
                     if (ok) held |= 1ull << k; else fail = true;
                 }
-                if (!fail) __threadfence();
+                if (!fail) fence_acq_rel();
             }
             if (!fail) {
                 const ulonglong2 v = Work::load(a, d);
@@ -225,7 +225,7 @@ __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
                 const uint32_t j = L.lig + k * L.G;
                 if (Work::writes(S.desc[j])) Work::store(a, S.desc[j], S.newv[j], first + j);
             }
-        __threadfence();
+        fence_acq_rel();
         order_key = ts;
     }
     for (uint32_t k = 0; k < kmax; ++k)
@@ -273,7 +273,7 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
                     // it goes out together with the value load
                     max64(rts_word, ts);
                     const ulonglong2 v = Work::load(a, d);
-                    __threadfence();
+                    fence_acq_rel();
                     if (ld_relaxed(wts_word) == y1) { S.oldv[j] = v; break; }
                     if (tries >= a.read_retries) { fail = true; break; }
                 }
@@ -290,7 +290,7 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
                 }
                 if (ok) {
                     held |= 1ull << k;
-                    __threadfence();
+                    fence_acq_rel();
                     const ulonglong2 v = Work::load(a, d);
                     S.oldv[j] = v;
                     S.newv[j] = Work::compute(a, d, v, a.operands[first + j]);
@@ -310,7 +310,7 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
                 const uint32_t j = L.lig + k * L.G;
                 Work::store(a, S.desc[j], S.newv[j], first + j);
             }
-        __threadfence();
+        fence_acq_rel();
         for (uint32_t k = 0; k < kmax; ++k)
             if (held >> k & 1)
                 st_relaxed(reinterpret_cast<uint64_t*>(&words[Work::rec(a, S.desc[L.lig + k * L.G])].y), ts);
@@ -370,7 +370,7 @@ __device__ int det_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
             const ulonglong2 v = Work::load(a, d);
             S.oldv[j] = v;
             if (w) Work::store(a, d, Work::compute(a, d, v, a.operands[first + j]), first + j);
-            __threadfence();
+            fence_acq_rel();
             add64(m, w ? DET_WRITE_DONE : DET_READ_DONE);
         }
     }
