@@ -173,6 +173,18 @@ typedef struct gcc_exec_params {
                                   record's chain by prefix sums [default]; 1 = run
                                   op by op, each op waiting for its predecessors
                                   (order-entry batches always run op by op) */
+    uint32_t retry_queue;      /* 2PL/TO/OCC: 1 = an aborted transaction that
+                                  conflicted on a record waits, holding nothing,
+                                  in a FIFO queue for that record and re-attempts
+                                  when served [1]; 2 = off (randomized backoff
+                                  after every abort) */
+    uint32_t queue_turn_ns;    /* estimated time per queue turn: a waiter n
+                                  turns from its own sleeps about n - 1 turns
+                                  before looking again [1000] */
+    uint32_t queue_width;      /* transactions a retry queue lets attempt at
+                                  once [1] */
+    uint32_t queue_after;      /* aborts of a transaction before it uses retry
+                                  queues; 1 = from its first abort [16] */
     uint32_t reserved;         /* 0 */
 } gcc_exec_params;
 
@@ -472,6 +484,44 @@ gcc_status gcc_det_execute_noalloc(void *d_table, uint32_t n_records, uint32_t n
                                    uint32_t n_ops, uint32_t max_ops_per_txn,
                                    gcc_txn_result *d_results, gcc_operand *d_reads,
                                    void *stream);
+
+/* Memory-system figures of one GPU, measured with the PTX operations the
+ * schemes use.  They are the denominators of the execute kernels' rooflines:
+ * bandwidth (random sectors, atomics on distinct words) when records are
+ * spread, and the latency of one contended record when hot records serialise
+ * their writers (Sec. IV-C finds contention decisive: every serializable
+ * read-modify-write chain on one record pays its protocol's round trips once
+ * per link).  The paper has no such call. */
+typedef struct gcc_memory_probe {
+    double hbm_load_ns;        /* dependent relaxed loads of lines not in L2 */
+    double l2_load_ns;         /* dependent relaxed loads of L2-resident lines */
+    double l2_load_acquire_ns; /* the same with acquire loads */
+    double l2_atomic_ns;       /* dependent atomicAdd(0) on L2-resident words */
+    double l2_cas_ns;          /* dependent (failing) 64-bit CAS on L2-resident words */
+    double gather32_gbs;       /* random 32-byte sectors of a 1 GiB buffer, all SMs, GB/s */
+    double cas_distinct_gops;  /* successful 64-bit CAS, one word per 32 B sector and
+                                  thread, all SMs, 1e9 per second */
+    double add_same_gops;      /* atomicAdd on one word, one lane per warp, all SMs */
+    double lock_handoff_ns;    /* one lock word: test, CAS acquire, release
+                                  store; ns per acquisition, best over 2, 16,
+                                  sm_count and `contenders` contending warps */
+    double occ_cycle_ns;       /* one record under the OCC commit sequence (acquire
+                                  version, read value, CAS lock, fence, ticket, write,
+                                  fence, publish); ns per commit, best over the
+                                  same contender counts */
+    double occ_cycle_busy_ns;  /* the same with `contenders` warps */
+    uint32_t sm_count;
+    uint32_t contenders;       /* 8 warps per SM (one lane each) */
+    uint32_t lock_best_contenders;  /* contending warps at lock_handoff_ns */
+    uint32_t occ_best_contenders;   /* contending warps at occ_cycle_ns */
+    uint64_t reserved[2];
+} gcc_memory_probe;
+
+/* Run the probes on `device` (about 0.3 s; allocates about 1.5 GiB for the
+ * duration, synchronous; the device becomes current on the calling thread).
+ * GCC_ERR_CUDA on a CUDA failure, GCC_ERR_DEVICE if a contended probe made
+ * no progress or lost an update. */
+gcc_status gcc_probe_memory(int device, gcc_memory_probe *out);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *gcc_last_error(void);

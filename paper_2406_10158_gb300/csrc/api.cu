@@ -67,6 +67,10 @@ gcc_exec_params defaults() {
     p.deadline_ns = 60000000000ull;
     p.seed = 0x5EEDull;
     p.inject_abort_ppm = 0;
+    p.retry_queue = 1;
+    p.queue_turn_ns = 1000;
+    p.queue_width = 1;
+    p.queue_after = 16;
     return p;
 }
 
@@ -87,6 +91,10 @@ gcc_exec_params merged(const gcc_exec_params* in) {
     if (in->seed) p.seed = in->seed;
     p.inject_abort_ppm = in->inject_abort_ppm;
     p.det_dataflow = in->det_dataflow;
+    if (in->retry_queue) p.retry_queue = in->retry_queue;
+    if (in->queue_turn_ns) p.queue_turn_ns = in->queue_turn_ns;
+    if (in->queue_width) p.queue_width = in->queue_width;
+    if (in->queue_after) p.queue_after = in->queue_after;
     return p;
 }
 
@@ -120,6 +128,7 @@ void free_db(gcc_db* db) {
     cudaFree(db->meta);
     cudaFree(db->st);
     cudaFree(db->dbs);
+    cudaFree(db->rq);
     cudaFree(db->sort.k0);
     cudaFree(db->sort.v0);
     cudaFree(db->sort.k1);
@@ -198,6 +207,7 @@ gcc_status create_impl(const gcc_db_desc* desc, gcc_db** out) {
     if ((s = dev_alloc(&db->meta, db->n_meta * 16, "control words (16 bytes per record for TO)"))) return bail(s);
     if ((s = dev_alloc(&db->st, sizeof(gcc::BatchState), "batch state"))) return bail(s);
     if ((s = dev_alloc(&db->dbs, sizeof(gcc::DbState), "db state"))) return bail(s);
+    if ((s = dev_alloc(&db->rq, (uint64_t)gcc::RETRY_QUEUES * 8, "retry queues"))) return bail(s);
     const uint64_t items = std::max<uint64_t>(d.max_batch_ops, d.max_batch_txns);
     db->sort.max_items = items;
     if ((s = dev_alloc(&db->sort.k0, items * 4, "sort keys"))) return bail(s);
@@ -233,6 +243,7 @@ gcc_status validate_params(const gcc_exec_params& p) {
     if (p.warps_per_block == 0 || p.warps_per_block > 32)
         return fail(GCC_ERR_INVALID, "warps_per_block must be in 1..32");
     if (p.collapse > 2) return fail(GCC_ERR_INVALID, "collapse must be 0, 1 or 2");
+    if (p.retry_queue > 2) return fail(GCC_ERR_INVALID, "retry_queue must be 0, 1 or 2");
     return GCC_OK;
 }
 
@@ -304,6 +315,11 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     a.wait_budget_ns = p.wait_budget_ns;
     a.deadline_ns = p.deadline_ns;
     a.seed = p.seed;
+    a.rq = (p.retry_queue == 2 || p.immediate_restart) ? nullptr : db->rq;
+    a.rq_mask = gcc::RETRY_QUEUES - 1;
+    a.queue_turn_ns = p.queue_turn_ns;
+    a.queue_width = p.queue_width;
+    a.queue_after = p.queue_after;
 
     GCC_CK(gcc::launch_batch_begin(db->st, db->dbs, scheme, st));
     launches += 1;
@@ -348,6 +364,8 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     const int64_t needed = ((int64_t)n_txns + slots - 1) / slots;
     grid = std::max<int64_t>(1, std::min(grid, needed));
     GCC_CK(cudaEventRecord(rec.ev[1], st));
+    if (n_txns && a.rq)
+        GCC_CK(cudaMemsetAsync(db->rq, 0, (size_t)gcc::RETRY_QUEUES * 8, st));
     if (n_txns) {
         GCC_CK(kv ? gcc::launch_kv_exec(scheme, db->d.field_bytes, a, (int)grid, block, smem, st)
                   : gcc::launch_oe_exec(scheme, a, (int)grid, block, smem, st));

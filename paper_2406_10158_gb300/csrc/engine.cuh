@@ -47,6 +47,9 @@ struct BatchState {
     unsigned int pad;
 };
 
+// Retry queues per database (one 64-bit word each).
+constexpr uint32_t RETRY_QUEUES = 1u << 16;
+
 // Persistent per-database device state.
 struct DbState {
     unsigned long long occ_clock;    // OCC commit timestamps, never reset
@@ -222,6 +225,11 @@ struct ExecArgs {
     uint64_t wait_budget_ns;
     uint64_t deadline_ns;
     uint64_t seed;
+    uint64_t* rq;               // retry queues (null: randomized backoff only)
+    uint32_t rq_mask;           // queues - 1 (a power of two)
+    uint32_t queue_turn_ns;     // estimated time per queue turn
+    uint32_t queue_width;       // tickets a queue admits at once
+    uint32_t queue_after;       // aborts before a transaction uses the queues
 };
 
 // Shared-memory staging per op: descriptor, observed word, value read and

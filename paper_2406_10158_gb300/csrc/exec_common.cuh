@@ -81,6 +81,14 @@ __device__ __forceinline__ bool injected_abort(const ExecArgs& a, uint32_t t, ui
     return (uint32_t)(h % 1000000ull) < a.inject_ppm;
 }
 
+// The record an aborted attempt conflicted on (the lowest failing lane's), or
+// NO_CC when it aborted for another reason.  Called by every lane of the group.
+__device__ __forceinline__ uint32_t group_conflict(const Lane& L, uint32_t frec) {
+    const unsigned b = __ballot_sync(L.gmask, frec != NO_CC);
+    if (!b) return NO_CC;
+    return __shfl_sync(L.gmask, frec, __ffs(b) - 1);
+}
+
 __device__ __forceinline__ unsigned long long group_ticket(const Lane& L, unsigned long long* ctr) {
     unsigned long long v = 0;
     if (L.lig == 0) v = agg_ticket(ctr);
@@ -93,9 +101,10 @@ __device__ __forceinline__ unsigned long long group_ticket(const Lane& L, unsign
 template <class Work>
 __device__ int occ_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint32_t t,
                            uint64_t first, uint32_t nops, uint32_t attempt,
-                           unsigned long long& order_key) {
+                           unsigned long long& order_key, uint32_t& crec) {
     const uint32_t kmax = (nops + L.G - 1) / L.G;
     bool fail = false;
+    uint32_t frec = NO_CC;   // this lane's conflicting record
     // read phase: consistent (version, value) pairs into the workspace
     for (uint32_t k = 0; k < kmax; ++k) {
         const uint32_t j = L.lig + k * L.G;
@@ -123,12 +132,15 @@ __device__ int occ_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
                         if (w) S.newv[j] = Work::compute(a, d, v, opd);
                         break;
                     }
-                    if (tries >= a.read_retries) { fail = true; break; }
+                    if (tries >= a.read_retries) { fail = true; frec = r; break; }
                     __nanosleep(32);
                 }
             }
         }
-        if (__any_sync(L.gmask, fail)) return ABORT;
+        if (__any_sync(L.gmask, fail)) {
+            crec = group_conflict(L, frec);
+            return ABORT;
+        }
     }
     // lock the write set, no waiting; a changed version fails the CAS too
     uint64_t held = 0;
@@ -138,7 +150,7 @@ __device__ int occ_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
             const uint32_t r = Work::rec(a, S.desc[j]);
             bool ok = !collapse_loser(a, r);
             if (ok) ok = cas64(a.meta + r, S.obs[j], S.obs[j] | OCC_LOCK) == S.obs[j];
-            if (ok) held |= 1ull << k; else fail = true;
+            if (ok) held |= 1ull << k; else { fail = true; frec = r; }
         }
         if (__any_sync(L.gmask, fail)) break;
     }
@@ -151,7 +163,7 @@ __device__ int occ_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
             const uint32_t j = L.lig + k * L.G;
             if (j < nops && !Work::writes(S.desc[j])) {
                 const uint32_t r = Work::rec(a, S.desc[j]);
-                if (r != NO_CC && ld_relaxed(a.meta + r) != S.obs[j]) fail = true;
+                if (r != NO_CC && ld_relaxed(a.meta + r) != S.obs[j]) { fail = true; frec = r; }
             }
         }
         if (!__any_sync(L.gmask, fail)) {
@@ -174,6 +186,7 @@ __device__ int occ_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
             const uint32_t j = L.lig + k * L.G;
             st_release(a.meta + Work::rec(a, S.desc[j]), S.obs[j]);
         }
+    crec = group_conflict(L, frec);
     return ABORT;
 }
 
@@ -183,9 +196,10 @@ __device__ int occ_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
 template <class Work>
 __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint32_t t,
                            uint64_t first, uint32_t nops, uint32_t attempt,
-                           unsigned long long& order_key) {
+                           unsigned long long& order_key, uint32_t& crec) {
     const uint32_t kmax = (nops + L.G - 1) / L.G;
     bool fail = false;
+    uint32_t frec = NO_CC;
     uint64_t held = 0;
     for (uint32_t k = 0; k < kmax; ++k) {
         const uint32_t j = L.lig + k * L.G;
@@ -197,14 +211,14 @@ __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
                 if (!Work::writes(d)) {
                     for (uint32_t tries = 0;; ++tries) {
                         const uint64_t w = ld_relaxed(m);
-                        if (w & TPL_X) { fail = true; break; }
+                        if (w & TPL_X) { fail = true; frec = r; break; }
                         if (cas64(m, w, w + TPL_S_ONE) == w) { held |= 1ull << k; break; }
-                        if (tries >= a.read_retries) { fail = true; break; }
+                        if (tries >= a.read_retries) { fail = true; frec = r; break; }
                     }
                 } else {
                     bool ok = !collapse_loser(a, r);
                     if (ok) ok = cas64(m, 0ull, TPL_X | (uint64_t)(t + 1)) == 0ull;
-                    if (ok) held |= 1ull << k; else fail = true;
+                    if (ok) held |= 1ull << k; else { fail = true; frec = r; }
                 }
                 if (!fail) fence_acq_rel();
             }
@@ -235,6 +249,7 @@ __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
             if (!Work::writes(S.desc[j])) add64(m, (uint64_t)0 - TPL_S_ONE);
             else st_release(m, 0ull);
         }
+    if (fail) crec = group_conflict(L, frec);
     return fail ? ABORT : COMMIT;
 }
 
@@ -244,11 +259,12 @@ __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
 template <class Work>
 __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint32_t t,
                           uint64_t first, uint32_t nops, uint32_t attempt,
-                          unsigned long long& order_key) {
+                          unsigned long long& order_key, uint32_t& crec) {
     const uint32_t kmax = (nops + L.G - 1) / L.G;
     const unsigned long long ts = group_ticket(L, &a.dbs->to_clock) + 1;
     ulonglong2* words = reinterpret_cast<ulonglong2*>(a.meta);
     bool fail = false;
+    uint32_t frec = NO_CC;
     uint64_t held = 0;
     for (uint32_t k = 0; k < kmax; ++k) {
         const uint32_t j = L.lig + k * L.G;
@@ -268,14 +284,14 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
                 uint64_t* rts_word = reinterpret_cast<uint64_t*>(&m->x);
                 for (uint32_t tries = 0;; ++tries) {
                     const uint64_t y1 = ld_acquire(wts_word);
-                    if ((y1 & TO_DIRTY) || ts < y1) { fail = true; break; }
+                    if ((y1 & TO_DIRTY) || ts < y1) { fail = true; frec = r; break; }
                     // raising RTS early only turns away older writers sooner, so
                     // it goes out together with the value load
                     max64(rts_word, ts);
                     const ulonglong2 v = Work::load(a, d);
                     fence_acq_rel();
                     if (ld_relaxed(wts_word) == y1) { S.oldv[j] = v; break; }
-                    if (tries >= a.read_retries) { fail = true; break; }
+                    if (tries >= a.read_retries) { fail = true; frec = r; break; }
                 }
             } else {
                 // write: needs ts > RTS and ts > WTS; mark dirty with WTS = ts
@@ -296,6 +312,7 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
                     S.newv[j] = Work::compute(a, d, v, a.operands[first + j]);
                 } else {
                     fail = true;
+                    frec = r;
                 }
             }
         }
@@ -322,6 +339,7 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
             const uint32_t j = L.lig + k * L.G;
             st_release(reinterpret_cast<uint64_t*>(&words[Work::rec(a, S.desc[j])].y), S.obs[j]);
         }
+    crec = group_conflict(L, frec);
     return ABORT;
 }
 
@@ -407,6 +425,35 @@ __device__ __forceinline__ uint32_t backoff_rounds(const ExecArgs& a, uint32_t t
     return (uint32_t)(mix64(a.seed ^ ((uint64_t)t << 24) ^ attempts) % (window + 1));
 }
 
+// Retry queues.  A transaction that has aborted queue_after times or more and
+// conflicted on a record backs off as above, then takes a ticket in the FIFO
+// queue that record hashes to and re-attempts when the queue admits its
+// ticket; it holds nothing while it waits, so the schemes'
+// attempts stay exactly as described above (no attempt ever waits for a
+// lock).  A queue admits the oldest `queue_width` unfinished tickets; an
+// admitted transaction counts its ticket finished when its attempt ends.  At
+// low contention a queue holds one transaction, which re-attempts at once;
+// on a hot record the aborted transactions re-attempt a few at a time instead
+// of all together.  A queue word is (tickets taken << 32) | tickets finished.
+// Admitted transactions always finish their attempt, so a queue never stalls;
+// a transaction still waiting at the kernel deadline gives up and abandons its
+// ticket, and the words are zeroed before every batch.
+constexpr uint32_t NO_Q = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t queue_of(const ExecArgs& a, uint32_t rec) {
+    return (uint32_t)mix64(rec) & a.rq_mask;
+}
+
+// Rounds a waiter sleeps before looking again, `ahead` turns from its own:
+// about one estimated turn per transaction ahead, so a queue word is read a
+// few times per turn however long the queue.
+__device__ __forceinline__ uint32_t queue_rounds(const ExecArgs& a, uint32_t ahead) {
+    const uint64_t q = a.backoff_base_ns ? a.backoff_base_ns : 128u;
+    uint64_t r = (uint64_t)(ahead - 1) * a.queue_turn_ns / q;
+    const uint64_t cap = a.backoff_cap_ns / q;
+    return (uint32_t)(r < cap ? r : cap);
+}
+
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
@@ -446,8 +493,10 @@ template <int SCHEME, class Work, class Fetch>
 __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, uint64_t deadline,
                            Counters& c) {
     constexpr bool DENSE = SCHEME == GCC_NO_WAIT_2PL || SCHEME == GCC_DET;
-    bool finished = false, has = false;
+    bool finished = false, has = false, served = false;
     uint32_t t = 0, nops = 0, attempts = 0, wait = 0;
+    uint32_t qi = NO_Q, qt = 0;   // retry queue and ticket while queued
+    uint32_t pq = NO_Q;           // queue to join once the backoff is over
     uint64_t first = 0;
     const ExecArgs* A = nullptr;
 
@@ -499,22 +548,63 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
         }
         if (__all_sync(0xffffffffu, finished)) break;
 
-        // 2. one attempt per group holding a transaction and not backing off
-        const bool go = has && wait == 0;
-        if (has && wait > 0) --wait;
-        if (go) {
+        // 2. one attempt per group holding a transaction that is neither
+        // backing off nor waiting for its turn in a retry queue
+        bool go = false, expired = false;
+        if (has && wait > 0) {
+            --wait;
+        } else if (has && (pq != NO_Q || (qi != NO_Q && !served))) {
             const ExecArgs& a = *A;
-            ++attempts;
+            uint64_t w = 0;
+            if (pq != NO_Q) {
+                // the backoff is over: take a ticket; the word before it
+                // also tells how many tickets have finished
+                qi = pq;
+                pq = NO_Q;
+                if (L.lig == 0) w = add64(a.rq + qi, 1ull << 32);
+                w = __shfl_sync(L.gmask, w, L.gbase);
+                qt = (uint32_t)(w >> 32);
+            } else {
+                if (L.lig == 0) w = ld_relaxed(a.rq + qi);
+                w = __shfl_sync(L.gmask, w, L.gbase);
+            }
+            // tickets taken before ours minus tickets finished; negative once
+            // later tickets finished first (queue_width > 1)
+            const int32_t ahead = (int32_t)(qt - (uint32_t)w);
+            if (ahead < (int32_t)a.queue_width) {
+                served = go = true;
+            } else if (globaltimer() > deadline) {
+                expired = true;                // the ticket is abandoned
+                qi = NO_Q;
+            } else {
+                wait = queue_rounds(a, (uint32_t)(ahead - (int32_t)a.queue_width + 1));
+            }
+        } else if (has) {
+            go = true;
+        }
+        if (go || expired) {
+            const ExecArgs& a = *A;
             unsigned long long order_key = 0;
-            int outcome;
-            if constexpr (SCHEME == GCC_OCC)
-                outcome = occ_attempt<Work>(a, L, S, t, first, nops, attempts, order_key);
-            else if constexpr (SCHEME == GCC_NO_WAIT_2PL)
-                outcome = tpl_attempt<Work>(a, L, S, t, first, nops, attempts, order_key);
-            else if constexpr (SCHEME == GCC_TO)
-                outcome = to_attempt<Work>(a, L, S, t, first, nops, attempts, order_key);
-            else
-                outcome = det_attempt<Work>(a, L, S, t, first, nops, order_key);
+            uint32_t crec = NO_CC;
+            int outcome = GIVE_UP;
+            if (go) {
+                ++attempts;
+                if constexpr (SCHEME == GCC_OCC)
+                    outcome = occ_attempt<Work>(a, L, S, t, first, nops, attempts, order_key, crec);
+                else if constexpr (SCHEME == GCC_NO_WAIT_2PL)
+                    outcome = tpl_attempt<Work>(a, L, S, t, first, nops, attempts, order_key, crec);
+                else if constexpr (SCHEME == GCC_TO)
+                    outcome = to_attempt<Work>(a, L, S, t, first, nops, attempts, order_key, crec);
+                else
+                    outcome = det_attempt<Work>(a, L, S, t, first, nops, order_key);
+            } else if (L.lig == 0) {
+                atomicOr(&a.st->error, GCC_DEVERR_DEADLINE);
+            }
+            if (served) {                      // pass the queue's turn on
+                if (L.lig == 0) add64(a.rq + qi, 1ull);
+                served = false;
+                qi = NO_Q;
+            }
             if (outcome == ABORT) {
                 if (L.lig == 0) ++c.aborts;
                 if (attempts >= a.max_attempts) {
@@ -524,7 +614,12 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
                     if (L.lig == 0) atomicOr(&a.st->error, GCC_DEVERR_DEADLINE);
                     outcome = GIVE_UP;
                 } else {
+                    // randomized backoff first (it breaks the symmetry of two
+                    // transactions that keep aborting each other), then the
+                    // queue of the record it conflicted on
                     wait = backoff_rounds(a, t, attempts);
+                    if (a.rq && crec != NO_CC && attempts >= a.queue_after)
+                        pq = queue_of(a, crec);
                 }
             }
             if (outcome == COMMIT) {

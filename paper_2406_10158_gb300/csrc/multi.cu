@@ -114,6 +114,13 @@ __global__ void multi_begin(const ExecArgs* __restrict__ args, DbState* const* _
     }
 }
 
+// Zeroes every database's retry queues (grid: queue words x databases).
+__global__ void multi_rq_reset(const ExecArgs* __restrict__ args, uint32_t n) {
+    const uint32_t i = blockIdx.y;
+    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && args[i].rq && w < RETRY_QUEUES) args[i].rq[w] = 0;
+}
+
 // Every database continues its own clock from the shared one.
 __global__ void multi_end(DbState* const* __restrict__ own, uint32_t n, const MultiState* ms) {
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -244,6 +251,8 @@ MetaState state_after(gcc_scheme s) {
 gcc_status enqueue(gcc_multi_plan* pl, cudaStream_t st) {
     using namespace gcc;
     multi_begin<<<1, 256, 0, st>>>(pl->d_args, pl->d_own, pl->n, pl->d_ms, (int)pl->scheme);
+    if (pl->n)
+        multi_rq_reset<<<dim3(RETRY_QUEUES / 256, pl->n), 256, 0, st>>>(pl->d_args, pl->n);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
         const uint32_t lanes = pl->p.lanes_per_txn;
@@ -266,7 +275,7 @@ gcc_status enqueue(gcc_multi_plan* pl, cudaStream_t st) {
                 break;
         }
     }
-    uint32_t launches = 2;
+    uint32_t launches = 3;
     if (e == cudaSuccess && pl->scheme != GCC_NO_WAIT_2PL && pl->total) {
         multi_rank_keys<<<blocks_for(pl->total, 256), 256, 0, st>>>(pl->d_args, pl->d_prefix, pl->n,
                                                                  pl->total, pl->sort.k0, pl->sort.v0);
@@ -396,6 +405,11 @@ gcc_status gcc_multi_plan_create(gcc_scheme scheme, const gcc_multi_batch* b, ui
         a.wait_budget_ns = p.wait_budget_ns;
         a.deadline_ns = p.deadline_ns;
         a.seed = p.seed ^ (0x9E3779B97F4A7C15ull * (i + 1));
+        a.rq = (p.retry_queue == 2 || p.immediate_restart) ? nullptr : db->rq;
+        a.rq_mask = gcc::RETRY_QUEUES - 1;
+        a.queue_turn_ns = p.queue_turn_ns;
+        a.queue_width = p.queue_width;
+        a.queue_after = p.queue_after;
         // control words in a state this scheme can start from
         if ((s = prepare_meta(db, scheme, pl->stream))) return bail(s);
         db->meta_state = state_after(scheme);

@@ -73,6 +73,7 @@ struct gcc_db {
     uint64_t n_meta = 0;
     gcc::BatchState* st = nullptr;
     gcc::DbState* dbs = nullptr;
+    uint64_t* rq = nullptr;             // retry queues (gcc::RETRY_QUEUES words)
     MetaState meta_state = META_ZERO;
     // scratch
     gcc::SortScratch sort{};

@@ -46,6 +46,8 @@ class ExecParams(ctypes.Structure):
                 ("wait_budget_ns", ctypes.c_uint64), ("deadline_ns", ctypes.c_uint64),
                 ("seed", ctypes.c_uint64), ("inject_abort_ppm", ctypes.c_uint32),
                 ("immediate_restart", ctypes.c_uint32), ("det_dataflow", ctypes.c_uint32),
+                ("retry_queue", ctypes.c_uint32), ("queue_turn_ns", ctypes.c_uint32),
+                ("queue_width", ctypes.c_uint32), ("queue_after", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
 
 
@@ -122,6 +124,18 @@ class Completion(ctypes.Structure):
                 ("arrival_ns", ctypes.c_uint64), ("done_ns", ctypes.c_uint64)]
 
 
+class MemoryProbe(ctypes.Structure):
+    _fields_ = [("hbm_load_ns", ctypes.c_double), ("l2_load_ns", ctypes.c_double),
+                ("l2_load_acquire_ns", ctypes.c_double), ("l2_atomic_ns", ctypes.c_double),
+                ("l2_cas_ns", ctypes.c_double), ("gather32_gbs", ctypes.c_double),
+                ("cas_distinct_gops", ctypes.c_double), ("add_same_gops", ctypes.c_double),
+                ("lock_handoff_ns", ctypes.c_double), ("occ_cycle_ns", ctypes.c_double),
+                ("occ_cycle_busy_ns", ctypes.c_double),
+                ("sm_count", ctypes.c_uint32), ("contenders", ctypes.c_uint32),
+                ("lock_best_contenders", ctypes.c_uint32), ("occ_best_contenders", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint64 * 2)]
+
+
 COMPLETION_DTYPE = np.dtype([("request", "<u8"), ("lane", "<u4"), ("status", "<u4"),
                              ("batch_seq", "<u8"), ("commit_order", "<u8"),
                              ("arrival_ns", "<u8"), ("done_ns", "<u8")])
@@ -180,6 +194,7 @@ SIGNATURES = {
     "gcc_det_execute_noalloc": (ctypes.c_int, [P, ctypes.c_uint32, ctypes.c_uint32,
                                                ctypes.c_uint32, P, ctypes.c_uint32, P, P,
                                                ctypes.c_uint32, ctypes.c_uint32, P, P, P]),
+    "gcc_probe_memory": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(MemoryProbe)]),
     "gcc_last_error": (ctypes.c_char_p, []),
 }
 
@@ -314,6 +329,13 @@ def gcc_autotune(db: int, scheme, txns_ptr: int, n_txns: int, ops_ptr: int, oper
                                ctypes.byref(space) if space is not None else None,
                                ctypes.byref(best), ctypes.byref(rep), stream or None))
     return best, {k: getattr(rep, k) for k, _ in rep._fields_}
+
+
+def gcc_probe_memory(device: int = 0) -> dict:
+    """Memory-system figures of `device` (latencies in ns, rates per second)."""
+    m = MemoryProbe()
+    _check(load().gcc_probe_memory(device, ctypes.byref(m)))
+    return {k: getattr(m, k) for k, _ in m._fields_ if k != "reserved"}
 
 
 def gcc_multi_plan_create(scheme, batches, p: Optional[ExecParams] = None) -> int:

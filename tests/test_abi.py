@@ -61,6 +61,7 @@ def test_struct_layouts_match_c(tmp_path):
     structs = {"gcc_db_desc": eng.DbDesc, "gcc_exec_params": eng.ExecParams,
                "gcc_batch_stats": eng.BatchStats, "gcc_stage_times": eng.StageTimes,
                "gcc_tune_space": eng.TuneSpace, "gcc_tune_report": eng.TuneReport,
+               "gcc_memory_probe": eng.MemoryProbe,
                "gcc_multi_batch": eng.MultiBatch, "gcc_server_lane": eng.ServerLane,
                "gcc_completion": eng.Completion}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gcc_gb300.h"', "int main(void){"]
