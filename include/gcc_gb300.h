@@ -184,7 +184,10 @@ typedef struct gcc_exec_params {
     uint32_t queue_width;      /* transactions a retry queue lets attempt at
                                   once [1] */
     uint32_t queue_after;      /* aborts of a transaction before it uses retry
-                                  queues; 1 = from its first abort [16] */
+                                  queues; 1 = from its first abort [2PL, TO:
+                                  16; OCC: 64 -- an OCC abort nearly always
+                                  means another transaction committed, so its
+                                  retries rarely need queueing] */
     uint32_t reserved;         /* 0 */
 } gcc_exec_params;
 

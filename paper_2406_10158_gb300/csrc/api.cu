@@ -70,8 +70,13 @@ gcc_exec_params defaults() {
     p.retry_queue = 1;
     p.queue_turn_ns = 1000;
     p.queue_width = 1;
-    p.queue_after = 16;
+    p.queue_after = 0;                   // per scheme, see queue_after_for
     return p;
+}
+
+uint32_t queue_after_for(const gcc_exec_params& p, gcc_scheme scheme) {
+    if (p.queue_after) return p.queue_after;
+    return scheme == GCC_OCC ? 64u : 16u;
 }
 
 gcc_exec_params merged(const gcc_exec_params* in) {
@@ -319,7 +324,7 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     a.rq_mask = gcc::RETRY_QUEUES - 1;
     a.queue_turn_ns = p.queue_turn_ns;
     a.queue_width = p.queue_width;
-    a.queue_after = p.queue_after;
+    a.queue_after = queue_after_for(p, scheme);
 
     GCC_CK(gcc::launch_batch_begin(db->st, db->dbs, scheme, st));
     launches += 1;

@@ -409,7 +409,7 @@ gcc_status gcc_multi_plan_create(gcc_scheme scheme, const gcc_multi_batch* b, ui
         a.rq_mask = gcc::RETRY_QUEUES - 1;
         a.queue_turn_ns = p.queue_turn_ns;
         a.queue_width = p.queue_width;
-        a.queue_after = p.queue_after;
+        a.queue_after = queue_after_for(p, scheme);
         // control words in a state this scheme can start from
         if ((s = prepare_meta(db, scheme, pl->stream))) return bail(s);
         db->meta_state = state_after(scheme);

@@ -39,6 +39,8 @@ constexpr uint32_t STAGE_RING = 256;
 // Library-internal helpers implemented in api.cu.
 gcc_exec_params defaults();
 gcc_exec_params merged(const gcc_exec_params* in);
+// Aborts before a transaction of `scheme` uses the retry queues.
+uint32_t queue_after_for(const gcc_exec_params& p, gcc_scheme scheme);
 gcc_status validate_params(const gcc_exec_params& p);
 gcc_status fail(gcc_status st, const char* fmt, ...);
 // Reset the control words if `scheme` cannot start from their current state.

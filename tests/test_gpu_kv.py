@@ -199,6 +199,50 @@ def test_attempt_budget_gives_up_cleanly(eng):
         check(table, db.read_kv(), batch, res, reads, "2pl", stats)
 
 
+@pytest.mark.parametrize("scheme", ["occ", "2pl", "to"])
+@pytest.mark.parametrize("policy", [dict(retry_queue=2), dict(queue_after=1),
+                                    dict(queue_after=1, queue_width=4),
+                                    dict(queue_after=3, queue_turn_ns=200)],
+                         ids=["off", "first-abort", "width4", "after3"])
+def test_retry_policies_replay(eng, scheme, policy):
+    """Zipf 0.99 over 4,096 records: with retry queues off, joined from the
+    first abort, admitting four at once, or joined after three aborts, every
+    txn commits and the history replays exactly."""
+    nrec = 1 << 12
+    table = wl.kv_table_splitmix(21, nrec, 2)
+    batch = wl.kv_batch(22, nrec=nrec, nfields=2, n_txns=4096, read_ratio=0.5, theta=0.99)
+    with eng.Database("kv", n_records=nrec, n_fields=2, field_bytes=8, max_batch_txns=4096) as db:
+        db.load_kv(table)
+        res, reads, stats = go(eng, db, scheme, batch, **HOT, **policy)
+        final = db.read_kv()
+    assert stats["committed"] == batch.n_txns, stats
+    check(table, final, batch, res, reads, scheme, stats)
+
+
+@pytest.mark.parametrize("scheme", ["occ", "2pl", "to"])
+def test_retry_queues_after_a_deadline(eng, scheme):
+    """A hot batch cut off by a 1 ms kernel deadline while transactions wait in
+    retry queues ends with TIMEOUT statuses and the deadline flag; what did
+    commit replays exactly, and the next batch on the database starts from
+    clean queues and commits everything."""
+    nrec = 1 << 10
+    table = wl.kv_table_splitmix(23, nrec, 2)
+    batch = wl.kv_batch(24, nrec=nrec, nfields=2, n_txns=16384, read_ratio=0.5, theta=0.99)
+    with eng.Database("kv", n_records=nrec, n_fields=2, field_bytes=8, max_batch_txns=16384) as db:
+        db.load_kv(table)
+        res, reads, stats = go(eng, db, scheme, batch, deadline_ns=1_000_000, queue_after=1)
+        state = db.read_kv()
+        if stats["timeouts"]:
+            assert "deadline" in stats["errors"], stats
+            assert (res["status"] == oracle.ST_TIMEOUT).sum() == stats["timeouts"]
+        assert stats["committed"] + stats["timeouts"] == batch.n_txns, stats
+        check(table, state, batch, res, reads, scheme, stats, require_all=False)
+        res, reads, stats = go(eng, db, scheme, batch, **HOT)
+        final = db.read_kv()
+    assert stats["committed"] == batch.n_txns, stats
+    check(state, final, batch, res, reads, scheme, stats)
+
+
 def test_det_wait_budget_returns(eng):
     """A deterministic-scheme wait that runs out of budget ends the batch with
     TIMEOUT statuses and an error flag instead of hanging; the database is
