@@ -413,16 +413,19 @@ __device__ void det_skip(const ExecArgs& a, const Lane& L, uint64_t first, uint3
     }
 }
 
-// Rounds an aborted transaction sits out: uniform in [0, window], the window
-// doubling with each abort up to backoff_cap_ns / backoff_base_ns.
-__device__ __forceinline__ uint32_t backoff_rounds(const ExecArgs& a, uint32_t t, uint32_t attempts) {
+// Nanoseconds an aborted transaction sits out: backoff_base_ns times a number
+// uniform in [0, window], the window doubling with each abort up to
+// backoff_cap_ns / backoff_base_ns.  Waits are deadlines on the global timer,
+// not round counts: a round lasts a few hundred nanoseconds in an idle warp
+// and several microseconds in a busy one.
+__device__ __forceinline__ uint64_t backoff_ns(const ExecArgs& a, uint32_t t, uint32_t attempts) {
     if (a.backoff_base_ns == 0) return 0;
     uint64_t cap = a.backoff_cap_ns / a.backoff_base_ns;
     if (cap < 1) cap = 1;
     const uint32_t sh = attempts - 1 < 20 ? attempts - 1 : 20;
     uint64_t window = 1ull << sh;
     if (window > cap) window = cap;
-    return (uint32_t)(mix64(a.seed ^ ((uint64_t)t << 24) ^ attempts) % (window + 1));
+    return (mix64(a.seed ^ ((uint64_t)t << 24) ^ attempts) % (window + 1)) * a.backoff_base_ns;
 }
 
 // Retry queues.  A transaction that has aborted queue_after times or more and
@@ -444,14 +447,12 @@ __device__ __forceinline__ uint32_t queue_of(const ExecArgs& a, uint32_t rec) {
     return (uint32_t)mix64(rec) & a.rq_mask;
 }
 
-// Rounds a waiter sleeps before looking again, `ahead` turns from its own:
-// about one estimated turn per transaction ahead, so a queue word is read a
-// few times per turn however long the queue.
-__device__ __forceinline__ uint32_t queue_rounds(const ExecArgs& a, uint32_t ahead) {
-    const uint64_t q = a.backoff_base_ns ? a.backoff_base_ns : 128u;
-    uint64_t r = (uint64_t)(ahead - 1) * a.queue_turn_ns / q;
-    const uint64_t cap = a.backoff_cap_ns / q;
-    return (uint32_t)(r < cap ? r : cap);
+// Nanoseconds a waiter sleeps before looking again, `ahead` turns from its
+// own: about one estimated turn per transaction ahead, so a queue word is
+// read a few times per turn however long the queue.
+__device__ __forceinline__ uint64_t queue_wait_ns(const ExecArgs& a, uint32_t ahead) {
+    const uint64_t w = (uint64_t)(ahead - 1) * a.queue_turn_ns;
+    return w < a.backoff_cap_ns ? w : a.backoff_cap_ns;
 }
 
 // ---------------------------------------------------------------------------
@@ -494,7 +495,8 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
                            Counters& c) {
     constexpr bool DENSE = SCHEME == GCC_NO_WAIT_2PL || SCHEME == GCC_DET;
     bool finished = false, has = false, served = false;
-    uint32_t t = 0, nops = 0, attempts = 0, wait = 0;
+    uint32_t t = 0, nops = 0, attempts = 0;
+    uint64_t wake = 0;            // global-timer time before which the group waits
     uint32_t qi = NO_Q, qt = 0;   // retry queue and ticket while queued
     uint32_t pq = NO_Q;           // queue to join once the backoff is over
     uint64_t first = 0;
@@ -541,7 +543,7 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
                 } else {
                     has = true;
                     attempts = 0;
-                    wait = 0;
+                    wake = 0;
                 }
                 __syncwarp(L.gmask);
             }
@@ -551,8 +553,12 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
         // 2. one attempt per group holding a transaction that is neither
         // backing off nor waiting for its turn in a retry queue
         bool go = false, expired = false;
-        if (has && wait > 0) {
-            --wait;
+        // Every decision below must be the same on all lanes of a group (they
+        // meet in group-wide shuffles and votes), so a group reads the timer
+        // once, on its base lane.
+        const uint64_t now = __shfl_sync(0xffffffffu, globaltimer(), L.gbase);
+        if (has && now < wake) {
+            // backing off, or not yet due to look at its queue
         } else if (has && (pq != NO_Q || (qi != NO_Q && !served))) {
             const ExecArgs& a = *A;
             uint64_t w = 0;
@@ -573,11 +579,11 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
             const int32_t ahead = (int32_t)(qt - (uint32_t)w);
             if (ahead < (int32_t)a.queue_width) {
                 served = go = true;
-            } else if (globaltimer() > deadline) {
+            } else if (now > deadline) {
                 expired = true;                // the ticket is abandoned
                 qi = NO_Q;
             } else {
-                wait = queue_rounds(a, (uint32_t)(ahead - (int32_t)a.queue_width + 1));
+                wake = now + queue_wait_ns(a, (uint32_t)(ahead - (int32_t)a.queue_width + 1));
             }
         } else if (has) {
             go = true;
@@ -607,17 +613,18 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
             }
             if (outcome == ABORT) {
                 if (L.lig == 0) ++c.aborts;
+                const uint64_t t2 = __shfl_sync(L.gmask, globaltimer(), L.gbase);
                 if (attempts >= a.max_attempts) {
                     if (L.lig == 0) atomicOr(&a.st->error, GCC_DEVERR_ATTEMPTS);
                     outcome = GIVE_UP;
-                } else if (globaltimer() > deadline) {
+                } else if (t2 > deadline) {
                     if (L.lig == 0) atomicOr(&a.st->error, GCC_DEVERR_DEADLINE);
                     outcome = GIVE_UP;
                 } else {
                     // randomized backoff first (it breaks the symmetry of two
                     // transactions that keep aborting each other), then the
                     // queue of the record it conflicted on
-                    wait = backoff_rounds(a, t, attempts);
+                    wake = t2 + backoff_ns(a, t, attempts);
                     if (a.rq && crec != NO_CC && attempts >= a.queue_after)
                         pq = queue_of(a, crec);
                 }
@@ -646,10 +653,15 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
             }
             __syncwarp(L.gmask);
         }
-        // 3. a warp where nobody attempted this round sleeps one quantum
+        // 3. a warp where nobody attempted this round sleeps until its
+        // earliest wake-up (32 ns .. 1 us)
         if (!__any_sync(0xffffffffu, go)) {
-            const uint32_t q = A ? A->backoff_base_ns : 0u;
-            __nanosleep(q ? q : 32);
+            const uint64_t t1 = globaltimer();
+            uint32_t rel = 1000;
+            if (has && wake > t1) rel = wake - t1 < 1000 ? (uint32_t)(wake - t1) : 1000u;
+            else if (has || !finished) rel = 32;   // due now, or about to fetch
+            rel = __reduce_min_sync(0xffffffffu, rel);
+            __nanosleep(rel < 32 ? 32 : rel);
         }
     }
 }
@@ -693,7 +705,8 @@ __global__ void __launch_bounds__(1024) exec_kernel(const __grid_constant__ Exec
     Lane L;
     Stage S;
     setup_lanes(a.lanes, a.max_ops, L, S);
-    const uint64_t deadline = globaltimer() + a.deadline_ns;
+    // one deadline per warp: lanes must agree on every time comparison
+    const uint64_t deadline = __shfl_sync(0xffffffffu, globaltimer(), 0) + a.deadline_ns;
     Counters c;
     SingleFetch<SCHEME == GCC_DET ? 1u : 4u> F{&a};
     group_loop<SCHEME, Work>(F, L, S, a.max_ops, deadline, c);

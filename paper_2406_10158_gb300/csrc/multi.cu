@@ -84,7 +84,8 @@ multi_kernel(const ExecArgs* __restrict__ args, const uint32_t* __restrict__ pre
     Lane L;
     Stage S;
     setup_lanes(lanes, max_ops, L, S);
-    const uint64_t deadline = globaltimer() + deadline_ns;
+    // one deadline per warp: lanes must agree on every time comparison
+    const uint64_t deadline = __shfl_sync(0xffffffffu, globaltimer(), 0) + deadline_ns;
     Counters c;
     MultiFetch F{args, prefix_s, n, ms, &c, nullptr};
     group_loop<SCHEME, Work>(F, L, S, max_ops, deadline, c);
