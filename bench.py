@@ -52,10 +52,12 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--seed", type=int, default=0x5EED0002)
-    p.add_argument("--form", choices=["plain", "batched", "served"], default="plain",
+    p.add_argument("--form", choices=["plain", "batched", "served", "sweep"], default="plain",
                    help="plain: one batch per launch (the default line); batched: 64 "
                         "databases in one persistent launch vs 64 plain launches; served: "
-                        "continuous batching of a Poisson trace vs plain per-batch launches")
+                        "continuous batching of a Poisson trace vs plain per-batch launches; "
+                        "sweep: every scheme across the key-value contention levels and the "
+                        "order-entry warehouse counts")
     p.add_argument("--n-db", type=int, default=64)
     p.add_argument("--rates", default="1e5,1e6,1e7,1e8")
     p.add_argument("--requests", type=int, default=1 << 18)
@@ -576,6 +578,85 @@ def run_served(args, rank, world):
             "clocks": clocks.summary()}
 
 
+# ---------------------------------------------------------------------------
+# contention sweep: every scheme across the key-value and order-entry configs
+# ---------------------------------------------------------------------------
+def run_sweep(args, rank, world):
+    """Committed txns/s and abort rate of every scheme on the key-value
+    workload (2^24 x 10 x 16-byte slots, 2^20 txns x 16 ops) at Zipf theta in
+    {0, 0.6, 0.8, 0.99} x read ratio {0.5, 0.95}, and on the order-entry mix
+    (2^18 txns, 50/50 NewOrder/Payment) at W in {1, 8, 64}.  Batches are
+    device-resident; a batch's time is the sum of its stage events (control
+    words, [deterministic preprocessing], execute, commit ranks)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_10158_gb300 import engine as eng
+    from paper_2406_10158_gb300 import workload as wl
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    up = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.uint8).reshape(-1)).to(dev)
+    prm = eng.params(deadline_ns=int(args.scheme_deadline_s * 1e9))
+
+    def batch_ms(h):
+        return h["prep_ms"] + h["kernel_ms"] + h["order_ms"]
+
+    kv_rows, oe_rows = [], []
+    with ClockSampler(dev) as clocks:
+        for rr in (0.5, 0.95):
+            for theta in (0.0, 0.6, 0.8, 0.99):
+                table, batch = wl.ycsb_kv(args.seed + rank, theta=theta, read_ratio=rr)
+                db = eng.Database("kv", n_records=1 << 24, n_fields=10, field_bytes=16,
+                                  max_batch_txns=batch.n_txns, device=dev)
+                db.load_kv(table)
+                tx, op, od = up(batch.txns), up(batch.ops), up(batch.operands)
+                rs = torch.empty(batch.n_txns * 16, dtype=torch.uint8, device=dev)
+                rd = torch.empty(batch.n_ops * 16, dtype=torch.uint8, device=dev)
+                torch.cuda.synchronize(dev)
+                reps = 1 if theta >= 0.99 else 3
+                for scheme in SCHEMES:
+                    for _ in range(1 + reps):
+                        db.execute(scheme, tx, op, od, batch.n_txns, batch.n_ops, rs, rd, prm)
+                    hist = db.stage_history(reps)
+                    st = db.last_stats()
+                    ms = statistics.mean(batch_ms(h) for h in hist)
+                    kv_rows.append({"theta": theta, "read_ratio": rr, "scheme": scheme,
+                                    "committed_txn_per_s": st["committed"] / ms * 1e3,
+                                    "abort_rate": st["abort_rate"], "ms_per_batch": ms,
+                                    "all_committed": st["committed"] == batch.n_txns})
+                db.close()
+        for W in (1, 8, 64):
+            db0, batch, cap = wl.order_entry(W=W, n_txns=1 << 18)
+            db = eng.Database("oe", n_warehouses=W, order_cap=cap, max_ops_per_txn=33,
+                              max_batch_txns=batch.n_txns, max_batch_ops=batch.n_ops, device=dev)
+            tx, op, od = up(batch.txns), up(batch.ops), up(batch.operands)
+            rs = torch.empty(batch.n_txns * 16, dtype=torch.uint8, device=dev)
+            rd = torch.empty(batch.n_ops * 16, dtype=torch.uint8, device=dev)
+            for scheme in SCHEMES:
+                for _ in range(2):                 # a warm-up batch, then the timed one
+                    db.load_oe(db0)               # fresh order slots for the inserts
+                    torch.cuda.synchronize(dev)
+                    db.execute(scheme, tx, op, od, batch.n_txns, batch.n_ops, rs, rd, prm)
+                h = db.stage_history(1)[-1]
+                st = db.last_stats()
+                ms = batch_ms(h)
+                oe_rows.append({"W": W, "scheme": scheme,
+                                "committed_txn_per_s": st["committed"] / ms * 1e3,
+                                "abort_rate": st["abort_rate"], "ms_per_batch": ms,
+                                "all_committed": st["committed"] == batch.n_txns})
+            db.close()
+    head = next(r for r in kv_rows if r["theta"] == 0.8 and r["read_ratio"] == 0.5
+                and r["scheme"] == "occ")
+    return {"metric": METRIC, "form": "sweep", "value": head["committed_txn_per_s"],
+            "unit": "txn/s", "n_gpus": world, "steps": 3, "warmup": 1, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "kv 2^24 x 10 x 16 B, 2^20 txns x 16 ops, zipf {0,0.6,0.8,0.99}"
+                                   " x read ratio {0.5,0.95}; order-entry W {1,8,64}, 2^18 txns",
+                       "value_is": "occ at zipf 0.8, read ratio 0.5"},
+            "kv": kv_rows, "order_entry": oe_rows, "clocks": clocks.summary()}
+
+
 def main(argv=None):
     args = parse_args(argv)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -596,6 +677,8 @@ def main(argv=None):
         out = run_batched(args, rank, world)
     elif args.form == "served":
         out = run_served(args, rank, world)
+    elif args.form == "sweep":
+        out = run_sweep(args, rank, world)
     else:
         out = run_ours(args, rank, world, dist)
     if out is not None and rank == 0:
