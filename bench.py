@@ -158,6 +158,13 @@ def sector_bytes(batch) -> dict:
     return {"random": random, "stream": stream, "per_txn": (random + stream) / max(1, batch.n_txns)}
 
 
+# DRAM traffic (read + write bytes) of one execute-kernel launch, from the ncu
+# capture in profiles/occ_kv_exec_kernel_full_dram.md: valid only for that
+# kernel build and workload (OCC, default launch, 2^24 x 10 x 16 B, 2^20 txns,
+# Zipf 0.8, read ratio 0.5); None for anything else.
+CAPTURED_TRAFFIC = {("occ", 1 << 24, 1 << 20, 0.8, 0.5, 0, 0): 3.52e9 + 723.51e6}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -361,7 +368,9 @@ def run_ours(args, rank, world, dist):
     peak, peak_kind = measured_peaks()
     achieved = alg["bytes"] / (kernel_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4),
+                "traffic": CAPTURED_TRAFFIC.get((args.scheme, args.records, args.txns, args.theta,
+                                                 args.read_ratio, args.lanes, args.warps)),
                 "kernel": f"kv_exec_kernel<{args.scheme}>", "kernel_ms": round(kernel_ms, 4),
                 "algorithmic_bytes_per_launch": alg["bytes"],
                 "algorithmic_bytes_per_txn": round(alg["per_txn"], 1),
