@@ -169,10 +169,12 @@ typedef struct gcc_exec_params {
                                   with this probability per million [0] */
     uint32_t immediate_restart;/* 1 = restart an aborted transaction at once, with
                                   no delay (the paper's policy) [0] */
-    uint32_t det_dataflow;     /* GCC_DET on key-value batches: 0 = evaluate each
-                                  record's chain by prefix sums [default]; 1 = run
-                                  op by op, each op waiting for its predecessors
-                                  (order-entry batches always run op by op) */
+    uint32_t det_dataflow;     /* GCC_DET: 0 = evaluate each record's chain in one
+                                  pass over the batch's accesses sorted by record
+                                  (key-value: prefix sums; order-entry: one warp
+                                  per record applies its ops in id order)
+                                  [default]; 1 = run op by op in the execute
+                                  kernel, each op waiting for its predecessors */
     uint32_t retry_queue;      /* 2PL/TO/OCC: 1 = an aborted transaction that
                                   conflicted on a record waits, holding nothing,
                                   in a FIFO queue for that record and re-attempts

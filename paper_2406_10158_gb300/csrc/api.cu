@@ -225,11 +225,11 @@ gcc_status create_impl(const gcc_db_desc* desc, gcc_db** out) {
     if ((s = dev_alloc(&db->scan_tmp, gcc::scan_tmp_words(items) * 4, "scan scratch"))) return bail(s);
     if ((s = dev_alloc(&db->need, d.max_batch_ops * 4, "wait thresholds"))) return bail(s);
     if ((s = dev_alloc(&db->order_key, d.max_batch_txns * 8, "commit keys"))) return bail(s);
-    if (d.schema == GCC_SCHEMA_KV) {
-        if ((s = dev_alloc(&db->fold_flags, d.max_batch_txns * 8, "fold flags"))) return bail(s);
-        if ((s = dev_alloc(&db->fold_seg, gcc::fold_seg_bytes(d.max_batch_ops), "fold carries")))
-            return bail(s);
-    }
+    if ((s = dev_alloc(&db->fold_flags, d.max_batch_txns * 8, "validity flags and ranks")))
+        return bail(s);
+    if (d.schema == GCC_SCHEMA_KV &&
+        (s = dev_alloc(&db->fold_seg, gcc::fold_seg_bytes(d.max_batch_ops), "fold carries")))
+        return bail(s);
     db->n_h_states = 256;
     if (cudaMallocHost(&db->h_states, sizeof(gcc::BatchState) * db->n_h_states) != cudaSuccess)
         return bail(fail(GCC_ERR_NOMEM, "cannot allocate pinned batch states"));
@@ -337,6 +337,27 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
                                 db->fold_seg, st));
         const int bits = bit_length((uint64_t)db->d.n_fields * db->d.n_records);
         launches += 2 + 3 * ((bits + 7) / 8) + 4 + 1 + 3 + 2;
+        GCC_CK(cudaEventRecord(rec.ev[2], st));
+        GCC_CK(cudaEventRecord(rec.ev[3], st));
+        rec.stream = st;
+        rec.scheme = scheme;
+        rec.n_txns = n_txns;
+        rec.launches = launches;
+        rec.grid = 0;
+        rec.used = true;
+        db->n_stages++;                  // control words untouched
+        db->last_stream = st;
+        db->last_scheme = scheme;
+        db->last_n_txns = n_txns;
+        return GCC_OK;
+    }
+    // deterministic order-entry batches: every record chain in one pass
+    if (scheme == GCC_DET && !kv && !p.det_dataflow) {
+        const int bits = std::max(1, bit_length(db->n_meta));
+        GCC_CK(cudaEventRecord(rec.ev[1], st));
+        GCC_CK(gcc::det_serial_oe(a, db->sort, db->scan_tmp, db->fold_flags, db->need, bits,
+                                  db->sm_count, st));
+        launches += gcc::det_serial_oe_launches(bits);
         GCC_CK(cudaEventRecord(rec.ev[2], st));
         GCC_CK(cudaEventRecord(rec.ev[3], st));
         rec.stream = st;

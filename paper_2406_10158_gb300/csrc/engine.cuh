@@ -287,6 +287,13 @@ gcc_status set_error(gcc_status s, const char* msg);
 // Deterministic scheme on a key-value batch by segmented prefix sums; `flags`
 // holds 2 * n_txns words, `seg_tmp` fold_seg_bytes(n_ops) bytes.
 size_t fold_seg_bytes(size_t max_ops);
+// Deterministic order-entry batch: each record's accesses applied in id order
+// by one warp over the sorted access table (reads, final records, NewOrder
+// inserts, results, dense ranks, batch counters).  `flags` holds 2 * n_txns
+// words, `heads` n_ops words; key_bits covers n_meta.
+cudaError_t det_serial_oe(const ExecArgs& a, SortScratch& s, uint32_t* scan_tmp, uint32_t* flags,
+                          uint32_t* heads, int key_bits, int sm_count, cudaStream_t st);
+int det_serial_oe_launches(int key_bits);
 cudaError_t det_fold_kv(const ExecArgs& a, uint32_t field_bytes, SortScratch& s,
                         uint32_t* scan_tmp, uint32_t* flags, void* seg_tmp, cudaStream_t st);
 

@@ -13,7 +13,15 @@ import oracle
 from paper_2406_10158_gb300 import workload as wl
 
 pytestmark = pytest.mark.gpu
-SCHEMES = ["occ", "2pl", "to", "det"]
+SCHEMES = ["occ", "2pl", "to", "det", "det-dataflow"]
+
+
+def scheme_params(eng, scheme, **kw):
+    """"det-dataflow" is the deterministic scheme run op by op in the execute
+    kernel (order-entry batches otherwise take the per-record pass)."""
+    if scheme == "det-dataflow":
+        scheme, kw = "det", dict(kw, det_dataflow=1)
+    return scheme, (eng.params(**kw) if kw else None)
 
 
 @pytest.fixture(scope="module")
@@ -33,15 +41,16 @@ def run_and_check(eng, W, n_txns, scheme, seed=5, lanes=None):
                       max_batch_txns=n_txns, max_batch_ops=batch.n_ops) as db:
         db.load_oe(db0)
         # one lane per txn stages 32 txns x 33 ops per warp: one warp per block
-        p = eng.params(lanes_per_txn=lanes, warps_per_block=1 if lanes == 1 else 8) \
-            if lanes else None
+        kw = dict(lanes_per_txn=lanes, warps_per_block=1 if lanes == 1 else 8) if lanes else {}
+        name = scheme
+        scheme, p = scheme_params(eng, scheme, **kw)
         res, reads, stats = db.run(scheme, batch, p, timeout_s=300)
         final = db.read_oe()
     assert stats["committed"] == n_txns and stats["device_error"] == 0, stats
     rep = oracle.oe_replay_check(db0, final, W, cap, batch, res, reads)
     assert rep["ok"], (scheme, rep)
     assert oracle.oe_consistency(final, W, cap) == 0
-    if scheme == "det":
+    if name.startswith("det"):
         ref, ref_reads = oracle.oe_serial(db0, W, cap, batch)
         assert np.array_equal(res["commit_order"], np.arange(n_txns))
         assert all(np.array_equal(ref[c], final[c]) for c in wl.OE_COLUMNS)
@@ -74,17 +83,18 @@ def test_order_entry_rejects_malformed(eng):
     bad = wl.KVBatch(txns=txns, ops=ops, operands=batch.operands)
     with eng.Database("oe", n_warehouses=W, order_cap=cap, max_ops_per_txn=33,
                       max_batch_txns=64, max_batch_ops=batch.n_ops) as db:
-        for scheme in SCHEMES:
+        for name in SCHEMES:
             db.load_oe(db0)
-            res, reads, stats = db.run(scheme, bad)
+            scheme, p = scheme_params(eng, name)
+            res, reads, stats = db.run(scheme, bad, p)
             st = res["status"]
-            assert (st[[pay[0], pay[1], no[0]]] == oracle.ST_INVALID).all(), scheme
-            assert (np.delete(st, [pay[0], pay[1], no[0]]) == oracle.ST_COMMITTED).all(), scheme
+            assert (st[[pay[0], pay[1], no[0]]] == oracle.ST_INVALID).all(), name
+            assert (np.delete(st, [pay[0], pay[1], no[0]]) == oracle.ST_COMMITTED).all(), name
 
 
 @pytest.mark.slow
 @pytest.mark.parametrize("W", [1, 8, 64])
 def test_order_entry_full_size(eng, W):
     """2^18 txns, 50/50 NewOrder/Payment, every scheme (the paper's TPC-C shape)."""
-    for scheme in SCHEMES:
+    for scheme in ["occ", "2pl", "to", "det"] + (["det-dataflow"] if W > 1 else []):
         run_and_check(eng, W, 1 << 18, scheme, seed=wl.SEEDS[2])
