@@ -61,6 +61,8 @@ def parse_args(argv=None):
     p.add_argument("--n-db", type=int, default=64)
     p.add_argument("--rates", default="1e5,1e6,1e7,1e8")
     p.add_argument("--requests", type=int, default=1 << 18)
+    p.add_argument("--kv-scheme", default="det", choices=SCHEMES, help="served form: key-value lane")
+    p.add_argument("--oe-scheme", default="det", choices=SCHEMES, help="served form: order-entry lane")
     return p.parse_args(argv)
 
 
@@ -505,10 +507,11 @@ def run_batched(args, rank, world):
 # ---------------------------------------------------------------------------
 def run_served(args, rank, world):
     """Open-loop Poisson arrivals, 50/50 by count of key-value txns (2^24 x 8
-    u64, 16 ops, Zipf 0.8, 80% reads; deterministic scheme) and order-entry
-    txns (W = 8; OCC), at each offered rate: committed txns/s and p50/p99
-    latency (arrival to result on the host), against plain per-batch launches
-    of the same requests (submit, wait, next)."""
+    u64, 16 ops, Zipf 0.8, 80% reads) and order-entry txns (W = 8), each lane
+    under its own scheme (--kv-scheme, --oe-scheme; deterministic by default),
+    at each offered rate: committed txns/s and p50/p99 latency (arrival to
+    result on the host), against plain per-batch launches of the same requests
+    (submit, wait, next)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -526,7 +529,8 @@ def run_served(args, rank, world):
     lane_of = (rng.random(n) < 0.5).astype(np.uint32)
     trace = wl.interleave([kv, oe], lane_of)
     max_batch = 1 << 14
-    lanes_kv = ("det", max_batch)
+    lanes_kv = (args.kv_scheme, max_batch)
+    oe_scheme = args.oe_scheme
     results = []
     rates = [float(r) for r in args.rates.split(",")]
 
@@ -544,7 +548,7 @@ def run_served(args, rank, world):
             arrivals = wl.poisson_arrivals(wl.SEEDS[4] + int(rate), n, rate)
             dkv, doe = fresh()
             srv = eng.Server([(dkv, lanes_kv[0], max_batch, 0, 100_000, 4),
-                              (doe, "occ", max_batch, 0, 100_000, 4)])
+                              (doe, oe_scheme, max_batch, 0, 100_000, 4)])
             comp, _ = srv.run_trace(lane_of, trace, arrivals)
             tots = [srv.lane_totals(0), srv.lane_totals(1)]
             srv.close()
@@ -565,7 +569,7 @@ def run_served(args, rank, world):
         t0 = time.perf_counter()
         committed = 0
         for start in range(0, max(s.n_txns for s in subs), max_batch):
-            for l, (db, scheme) in enumerate(((dkv, lanes_kv[0]), (doe, "occ"))):
+            for l, (db, scheme) in enumerate(((dkv, lanes_kv[0]), (doe, oe_scheme))):
                 idx = np.arange(start, min(start + max_batch, subs[l].n_txns))
                 if idx.size:
                     _, _, st = db.run(scheme, wl.select(subs[l], idx))
@@ -579,7 +583,8 @@ def run_served(args, rank, world):
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"{n} requests, 50/50 kv (2^24 x 8 u64, 16 ops, zipf 0.8, 80% "
-                                   f"reads, det) and order-entry (W=8, occ), poisson arrivals",
+                                   f"reads, {lanes_kv[0]}) and order-entry (W=8, {oe_scheme}), "
+                                   f"poisson arrivals",
                        "max_batch_txns": max_batch, "max_delay_us": 100, "depth": 4},
             "p99_latency_us": best["p99_latency_us"], "rates": results,
             "plain_per_batch": {"value": committed / plain_s, "unit": "txn/s"},

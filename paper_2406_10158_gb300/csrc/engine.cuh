@@ -104,6 +104,35 @@ __device__ __forceinline__ ulonglong2 cas128(ulonglong2* p, ulonglong2 cmp, ulon
 __device__ __forceinline__ uint64_t cas64(uint64_t* p, uint64_t cmp, uint64_t val) {
     return atomicCAS(reinterpret_cast<unsigned long long*>(p), cmp, val);
 }
+// Lock acquisitions: acquire semantics order the caller's later accesses
+// (the locked record's value) after the CAS.
+__device__ __forceinline__ uint64_t cas64_acquire(uint64_t* p, uint64_t cmp, uint64_t val) {
+    uint64_t old;
+    asm volatile("atom.acquire.gpu.global.cas.b64 %0, [%1], %2, %3;"
+                 : "=l"(old) : "l"(p), "l"(cmp), "l"(val) : "memory");
+    return old;
+}
+__device__ __forceinline__ ulonglong2 cas128_acquire(ulonglong2* p, ulonglong2 cmp, ulonglong2 val) {
+    ulonglong2 old;
+    asm volatile(
+        "{\n\t.reg .b128 c, v, d;\n\t"
+        "mov.b128 c, {%2, %3};\n\t"
+        "mov.b128 v, {%4, %5};\n\t"
+        "atom.acquire.gpu.global.cas.b128 d, [%6], c, v;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t}"
+        : "=l"(old.x), "=l"(old.y)
+        : "l"(cmp.x), "l"(cmp.y), "l"(val.x), "l"(val.y), "l"(p)
+        : "memory");
+    return old;
+}
+// Lock releases and done-counters: release semantics order the caller's
+// earlier accesses before the update.
+__device__ __forceinline__ uint64_t add64_release(uint64_t* p, uint64_t v) {
+    uint64_t old;
+    asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;"
+                 : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
 __device__ __forceinline__ uint64_t max64(uint64_t* p, uint64_t v) {
     return atomicMax(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
@@ -145,6 +174,22 @@ __device__ __forceinline__ unsigned long long agg_ticket(unsigned long long* ctr
         base = atomicAdd(ctr, (unsigned long long)__popc(mask) * step);
     base = __shfl_sync(mask, base, leader);
     return base + (unsigned long long)__popc(mask & lanemask_lt()) * step;
+}
+// The same with an acquire-release atomic: the caller's earlier memory
+// operations are ordered before its ticket and its later ones after it, so a
+// thread whose ticket follows this one (the counter's read-modify-write chain
+// carries the release) also sees everything that preceded this ticket.
+__device__ __forceinline__ unsigned long long agg_ticket_acq_rel(unsigned long long* ctr) {
+    unsigned mask = __activemask();
+    int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if ((threadIdx.x & 31) == leader) {
+        const unsigned long long inc = (unsigned long long)__popc(mask);
+        asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;"
+                     : "=l"(base) : "l"(ctr), "l"(inc) : "memory");
+    }
+    base = __shfl_sync(mask, base, leader);
+    return base + (unsigned long long)__popc(mask & lanemask_lt());
 }
 
 // 64-bit mixing (splitmix64 finaliser) for jitter and abort injection.

@@ -94,6 +94,12 @@ __device__ __forceinline__ unsigned long long group_ticket(const Lane& L, unsign
     if (L.lig == 0) v = agg_ticket(ctr);
     return __shfl_sync(L.gmask, v, L.gbase);
 }
+__device__ __forceinline__ unsigned long long group_ticket_acq_rel(const Lane& L,
+                                                                   unsigned long long* ctr) {
+    unsigned long long v = 0;
+    if (L.lig == 0) v = agg_ticket_acq_rel(ctr);
+    return __shfl_sync(L.gmask, v, L.gbase);
+}
 
 // ---------------------------------------------------------------------------
 // OCC
@@ -156,8 +162,17 @@ __device__ int occ_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
     }
     fail = __any_sync(L.gmask, fail) || injected_abort(a, t, attempt);
     if (!fail) {
-        fence_acq_rel();
-        const unsigned long long ts = group_ticket(L, &a.dbs->occ_clock);
+        // The commit timestamp is an acquire-release atomic on the clock: its
+        // release half orders the write locks before it, its acquire half the
+        // validation and the writes after it.  Of two transactions, the one
+        // with the later timestamp therefore sees the other's locks: a record
+        // it validates that the other locked shows as locked (no write skew,
+        // no missed anti-dependency), and timestamp order is a serial order.
+        // One lane takes the group's timestamp; the warp barriers around it
+        // order the other lanes' locks before it and their reads after it.
+        __syncwarp(L.gmask);
+        const unsigned long long ts = group_ticket_acq_rel(L, &a.dbs->occ_clock);
+        __syncwarp(L.gmask);
         // validate the read set against the versions observed
         for (uint32_t k = 0; k < kmax; ++k) {
             const uint32_t j = L.lig + k * L.G;
@@ -173,10 +188,11 @@ __device__ int occ_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
                     const uint32_t j = L.lig + k * L.G;
                     Work::store(a, S.desc[j], S.newv[j], first + j);
                 }
-            fence_acq_rel();
+            // publish: a release store, so a reader that acquires the new
+            // version sees the values written before it
             for (uint32_t k = 0; k < kmax; ++k)
                 if (held >> k & 1)
-                    st_relaxed(a.meta + Work::rec(a, S.desc[L.lig + k * L.G]), ts + 1);
+                    st_release(a.meta + Work::rec(a, S.desc[L.lig + k * L.G]), ts + 1);
             order_key = ts;
             return COMMIT;
         }
@@ -212,15 +228,14 @@ __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
                     for (uint32_t tries = 0;; ++tries) {
                         const uint64_t w = ld_relaxed(m);
                         if (w & TPL_X) { fail = true; frec = r; break; }
-                        if (cas64(m, w, w + TPL_S_ONE) == w) { held |= 1ull << k; break; }
+                        if (cas64_acquire(m, w, w + TPL_S_ONE) == w) { held |= 1ull << k; break; }
                         if (tries >= a.read_retries) { fail = true; frec = r; break; }
                     }
                 } else {
                     bool ok = !collapse_loser(a, r);
-                    if (ok) ok = cas64(m, 0ull, TPL_X | (uint64_t)(t + 1)) == 0ull;
+                    if (ok) ok = cas64_acquire(m, 0ull, TPL_X | (uint64_t)(t + 1)) == 0ull;
                     if (ok) held |= 1ull << k; else { fail = true; frec = r; }
                 }
-                if (!fail) fence_acq_rel();
             }
             if (!fail) {
                 const ulonglong2 v = Work::load(a, d);
@@ -232,21 +247,23 @@ __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
     }
     fail = __any_sync(L.gmask, fail) || injected_abort(a, t, attempt);
     if (!fail) {
-        // lock point: every lock is held
+        // lock point: every lock is held.  The warp barriers order the group's
+        // lock acquisitions before the ticket and its releases after it.
+        __syncwarp(L.gmask);
         const unsigned long long ts = group_ticket(L, &a.st->ticket);
+        __syncwarp(L.gmask);
         for (uint32_t k = 0; k < kmax; ++k)
             if (held >> k & 1) {
                 const uint32_t j = L.lig + k * L.G;
                 if (Work::writes(S.desc[j])) Work::store(a, S.desc[j], S.newv[j], first + j);
             }
-        fence_acq_rel();
         order_key = ts;
     }
     for (uint32_t k = 0; k < kmax; ++k)
         if (held >> k & 1) {
             const uint32_t j = L.lig + k * L.G;
             uint64_t* m = a.meta + Work::rec(a, S.desc[j]);
-            if (!Work::writes(S.desc[j])) add64(m, (uint64_t)0 - TPL_S_ONE);
+            if (!Work::writes(S.desc[j])) add64_release(m, (uint64_t)0 - TPL_S_ONE);
             else st_release(m, 0ull);
         }
     if (fail) crec = group_conflict(L, frec);
@@ -300,13 +317,12 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
                 for (uint32_t tries = 0; ok; ++tries) {
                     const ulonglong2 w = ld_slot16(m);
                     if ((w.y & TO_DIRTY) || ts < w.x || ts < w.y) { ok = false; break; }
-                    const ulonglong2 o = cas128(m, w, make_ulonglong2(w.x, TO_DIRTY | ts));
+                    const ulonglong2 o = cas128_acquire(m, w, make_ulonglong2(w.x, TO_DIRTY | ts));
                     if (o.x == w.x && o.y == w.y) { S.obs[j] = w.y; break; }
                     if (tries >= a.read_retries) { ok = false; break; }
                 }
                 if (ok) {
                     held |= 1ull << k;
-                    fence_acq_rel();
                     const ulonglong2 v = Work::load(a, d);
                     S.oldv[j] = v;
                     S.newv[j] = Work::compute(a, d, v, a.operands[first + j]);
@@ -327,10 +343,9 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
                 const uint32_t j = L.lig + k * L.G;
                 Work::store(a, S.desc[j], S.newv[j], first + j);
             }
-        fence_acq_rel();
         for (uint32_t k = 0; k < kmax; ++k)
             if (held >> k & 1)
-                st_relaxed(reinterpret_cast<uint64_t*>(&words[Work::rec(a, S.desc[L.lig + k * L.G])].y), ts);
+                st_release(reinterpret_cast<uint64_t*>(&words[Work::rec(a, S.desc[L.lig + k * L.G])].y), ts);
         order_key = ts;
         return COMMIT;
     }
@@ -388,8 +403,7 @@ __device__ int det_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
             const ulonglong2 v = Work::load(a, d);
             S.oldv[j] = v;
             if (w) Work::store(a, d, Work::compute(a, d, v, a.operands[first + j]), first + j);
-            fence_acq_rel();
-            add64(m, w ? DET_WRITE_DONE : DET_READ_DONE);
+            add64_release(m, w ? DET_WRITE_DONE : DET_READ_DONE);
         }
     }
     if (__any_sync(L.gmask, fail)) return GIVE_UP;
