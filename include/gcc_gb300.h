@@ -49,7 +49,9 @@ typedef enum gcc_scheme {
     GCC_NO_WAIT_2PL = 0,   /* two-phase locking, abort when a lock is taken     */
     GCC_TO = 1,            /* basic timestamp ordering with a commit (dirty) bit */
     GCC_OCC = 2,           /* read-validate-write OCC with commit timestamps    */
-    GCC_DET = 3            /* deterministic conflict-ordered batch (GPUTx-like) */
+    GCC_DET = 3,           /* deterministic conflict-ordered batch (GPUTx-like) */
+    GCC_TICTOC = 4         /* OCC with timestamps computed from per-record write
+                              and read timestamps (TicToc, Table I) */
 } gcc_scheme;
 
 typedef enum gcc_schema {

@@ -261,6 +261,9 @@ gcc_status prepare_meta(gcc_db* db, gcc_scheme scheme, cudaStream_t st) {
         case GCC_OCC: reset = db->meta_state != META_ZERO && db->meta_state != META_OCC; break;
         case GCC_TO: reset = db->meta_state != META_ZERO && db->meta_state != META_TO; break;
         case GCC_DET: reset = false; break;    // per-record counters set by preprocessing
+        case GCC_TICTOC:
+            reset = db->meta_state != META_ZERO && db->meta_state != META_TICTOC;
+            break;
     }
     if (reset) GCC_CK(cudaMemsetAsync(db->meta, 0, db->n_meta * 16, st));
     return GCC_OK;
@@ -271,7 +274,7 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
                         const gcc_exec_params* params, gcc_txn_result* d_results,
                         gcc_operand* d_reads, cudaStream_t stream) {
     if (!db) return fail(GCC_ERR_INVALID, "null database");
-    if ((unsigned)scheme > GCC_DET) return fail(GCC_ERR_INVALID, "unknown scheme %d", (int)scheme);
+    if ((unsigned)scheme > GCC_TICTOC) return fail(GCC_ERR_INVALID, "unknown scheme %d", (int)scheme);
     if (n_txns > db->d.max_batch_txns || n_ops > db->d.max_batch_ops)
         return fail(GCC_ERR_CAPACITY, "batch of %u txns / %llu ops exceeds the database maxima",
                     n_txns, (unsigned long long)n_ops);
@@ -306,6 +309,7 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     a.order_cap = db->d.order_cap;
     a.need = db->need;
     a.order_key = db->order_key;
+    a.seq = db->fold_flags;
     a.order_key_uses_base = scheme == GCC_OCC || scheme == GCC_TO;
     a.st = db->st;
     a.dbs = db->dbs;
@@ -402,6 +406,10 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
         GCC_CK(gcc::densify_commit_order(a, db->sort, st));
         launches += 1 + 3 * 4 + 1;                           // emit, 4 sort passes, rank
     }
+    if (n_txns && scheme == GCC_TICTOC) {
+        GCC_CK(gcc::densify_tictoc(a, db->sort, st));
+        launches += 3 * (1 + 3 * 4) + 1;                     // 3 x (emit, 4 passes), rank
+    }
     GCC_CK(cudaEventRecord(rec.ev[3], st));
     rec.stream = st;
     rec.scheme = scheme;
@@ -415,6 +423,7 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
         case GCC_OCC: db->meta_state = META_OCC; break;
         case GCC_TO: db->meta_state = META_TO; break;
         case GCC_DET: db->meta_state = META_DET; break;
+        case GCC_TICTOC: db->meta_state = META_TICTOC; break;
     }
     db->last_stream = st;
     db->last_scheme = scheme;

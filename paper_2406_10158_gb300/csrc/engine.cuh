@@ -27,6 +27,10 @@ constexpr uint64_t TPL_S_ONE = 1ull << 32;
 // II packs commit bit + 31-bit RTS + 31-bit WTS into 8 bytes, which overflows
 // after 2^31 attempts; 64-bit timestamps from a persistent clock never do.
 constexpr uint64_t TO_DIRTY = 1ull << 63;
+// TicToc: one 16-byte word per record: lo = rts, hi = wts (bits 0..62) | lock
+// (bit 63).  The record's current version is valid over [wts, rts]; a commit
+// at timestamp c publishes wts = rts = c.
+constexpr uint64_t TT_LOCK = 1ull << 63;
 // DET: bits 32..63 ops completed on the record, bits 0..31 writes completed,
 // both counted from the record's first position in the batch's sorted
 // access table (Sec. III-E.3, "access tables").
@@ -254,7 +258,8 @@ struct ExecArgs {
     uint32_t order_cap;
     // scheme scratch
     const uint32_t* need;         // DET: per-op wait threshold
-    unsigned long long* order_key;// OCC/TO: raw commit timestamp per txn
+    unsigned long long* order_key;// OCC/TO/TicToc: raw commit timestamp per txn
+    uint32_t* seq;                // TicToc: commit sequence number per txn (ties)
     int order_key_uses_base;      // OCC: timestamps count from BatchState::ticket_base
     BatchState* st;
     DbState* dbs;
@@ -344,5 +349,7 @@ cudaError_t det_fold_kv(const ExecArgs& a, uint32_t field_bytes, SortScratch& s,
 
 // OCC / TO: replace raw commit timestamps by dense ranks 0..committed-1.
 cudaError_t densify_commit_order(const ExecArgs& a, SortScratch& s, cudaStream_t st);
+// TicToc: dense ranks in (timestamp, sequence number) order.
+cudaError_t densify_tictoc(const ExecArgs& a, SortScratch& s, cudaStream_t st);
 
 }  // namespace gcc

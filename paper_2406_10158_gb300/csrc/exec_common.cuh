@@ -33,6 +33,10 @@
 //    timestamp, validate the read set, write and release with the new version
 //    (Sec. II-B, Sec. III-E.2 Silo: lock bit + 63-bit timestamp, no epochs,
 //    no-wait locking).  Commit order: the timestamp.
+//  * TicToc       -- OCC whose commit timestamp is computed from per-record
+//    write and read timestamps instead of a shared clock; a read stays valid
+//    by extending its record's read timestamp (Table I lists TicToc among the
+//    CPU-oriented schemes).  Commit order: (timestamp, sequence number).
 //  * DET          -- every op waits until the lower-id accesses to its record
 //    that conflict with it are done, then runs; nothing aborts and the outcome
 //    is the serial execution in transaction-id order (Sec. II-C GPUTx;
@@ -359,6 +363,150 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
 }
 
 // ---------------------------------------------------------------------------
+// TicToc
+// ---------------------------------------------------------------------------
+// Maximum of a 64-bit value over the lanes of a group (groups are aligned
+// power-of-two sub-warps, so xor shuffles stay inside the group).
+__device__ __forceinline__ uint64_t group_max64(const Lane& L, uint64_t v) {
+    for (uint32_t off = L.G >> 1; off > 0; off >>= 1) {
+        const uint64_t o = __shfl_xor_sync(L.gmask, v, off);
+        v = o > v ? o : v;
+    }
+    return v;
+}
+
+// Read phase as OCC's, recording each record's wts and rts; the write set is
+// locked without waiting; the commit timestamp is computed, not drawn from a
+// clock: at least every record read's wts and one past every record written's
+// rts.  A record read whose observed rts already covers the timestamp needs
+// no check; otherwise its rts is extended to the timestamp with a 128-bit CAS
+// that also proves the version unchanged and unlocked.  Writes publish
+// wts = rts = timestamp.  Two commits never tie on a timestamp when they
+// conflict on a write-write or read-then-overwrite pair; the only tie is a
+// reader of a version at that version's own timestamp, and the writer's
+// sequence number, taken before it publishes, orders it first.  The serial
+// order is (timestamp, sequence number).
+template <class Work>
+__device__ int tictoc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint32_t t,
+                              uint64_t first, uint32_t nops, uint32_t attempt,
+                              unsigned long long& order_key, uint32_t& seq_out, uint32_t& crec) {
+    const uint32_t kmax = (nops + L.G - 1) / L.G;
+    ulonglong2* words = reinterpret_cast<ulonglong2*>(a.meta);
+    bool fail = false;
+    uint32_t frec = NO_CC;
+    // read phase: (wts, value, rts); a read op keeps its rts in newv.x
+    for (uint32_t k = 0; k < kmax; ++k) {
+        const uint32_t j = L.lig + k * L.G;
+        if (j < nops) {
+            const uint64_t d = S.desc[j];
+            const uint32_t r = Work::rec(a, d);
+            if (r == NO_CC) {
+                S.oldv[j] = Work::load(a, d);
+            } else {
+                ulonglong2* m = words + r;
+                uint64_t* wts_word = reinterpret_cast<uint64_t*>(&m->y);
+                uint64_t* rts_word = reinterpret_cast<uint64_t*>(&m->x);
+                const bool w = Work::writes(d);
+                const ulonglong2 opd = w ? a.operands[first + j] : make_ulonglong2(0ull, 0ull);
+                for (uint32_t tries = 0;; ++tries) {
+                    const uint64_t y1 = ld_acquire(wts_word);
+                    if (!(y1 & TT_LOCK)) {
+                        const ulonglong2 v = Work::load(a, d);
+                        S.obs[j] = y1;
+                        S.oldv[j] = v;
+                        if (w) S.newv[j] = Work::compute(a, d, v, opd);
+                        else S.newv[j] = make_ulonglong2(ld_relaxed(rts_word), 0ull);
+                        break;
+                    }
+                    if (tries >= a.read_retries) { fail = true; frec = r; break; }
+                    __nanosleep(32);
+                }
+            }
+        }
+        if (__any_sync(L.gmask, fail)) {
+            crec = group_conflict(L, frec);
+            return ABORT;
+        }
+    }
+    // lock the write set, no waiting; a changed wts fails the CAS too
+    uint64_t held = 0;
+    for (uint32_t k = 0; k < kmax; ++k) {
+        const uint32_t j = L.lig + k * L.G;
+        if (j < nops && Work::writes(S.desc[j])) {
+            const uint32_t r = Work::rec(a, S.desc[j]);
+            uint64_t* wts_word = reinterpret_cast<uint64_t*>(&words[r].y);
+            bool ok = !collapse_loser(a, r);
+            if (ok) ok = cas64_acquire(wts_word, S.obs[j], S.obs[j] | TT_LOCK) == S.obs[j];
+            if (ok) held |= 1ull << k; else { fail = true; frec = r; }
+        }
+        if (__any_sync(L.gmask, fail)) break;
+    }
+    fail = __any_sync(L.gmask, fail) || injected_abort(a, t, attempt);
+    if (!fail) {
+        // the timestamp: a locked record's rts no longer moves (extensions
+        // need it unlocked)
+        uint64_t c = 0;
+        for (uint32_t k = 0; k < kmax; ++k) {
+            const uint32_t j = L.lig + k * L.G;
+            if (j < nops) {
+                const uint32_t r = Work::rec(a, S.desc[j]);
+                if (r == NO_CC) continue;
+                const uint64_t cand = Work::writes(S.desc[j])
+                    ? ld_relaxed(reinterpret_cast<uint64_t*>(&words[r].x)) + 1
+                    : S.obs[j];
+                c = cand > c ? cand : c;
+            }
+        }
+        const uint64_t ts = group_max64(L, c);
+        // the sequence number goes out together with the validation
+        __syncwarp(L.gmask);
+        unsigned long long sq = 0;
+        if (L.lig == 0) sq = agg_ticket_acq_rel(&a.st->ticket);
+        // validate the read set at the timestamp, extending rts where needed
+        for (uint32_t k = 0; k < kmax; ++k) {
+            const uint32_t j = L.lig + k * L.G;
+            if (j < nops && !Work::writes(S.desc[j])) {
+                const uint32_t r = Work::rec(a, S.desc[j]);
+                if (r == NO_CC || S.newv[j].x >= ts) continue;
+                ulonglong2* m = words + r;
+                bool ok = false;
+                for (uint32_t tries = 0; tries <= a.read_retries; ++tries) {
+                    const ulonglong2 w = ld_slot16(m);
+                    if (w.y != S.obs[j]) break;                  // written or locked since
+                    if (w.x >= ts) { ok = true; break; }
+                    const ulonglong2 o = cas128(m, w, make_ulonglong2(ts, w.y));
+                    if (o.x == w.x && o.y == w.y) { ok = true; break; }
+                }
+                if (!ok) { fail = true; frec = r; }
+            }
+        }
+        sq = __shfl_sync(L.gmask, sq, L.gbase);
+        __syncwarp(L.gmask);
+        if (!__any_sync(L.gmask, fail)) {
+            // write phase, then publish the version [ts, ts] and unlock
+            for (uint32_t k = 0; k < kmax; ++k)
+                if (held >> k & 1) {
+                    const uint32_t j = L.lig + k * L.G;
+                    Work::store(a, S.desc[j], S.newv[j], first + j);
+                    ulonglong2* m = words + Work::rec(a, S.desc[j]);
+                    st_relaxed(reinterpret_cast<uint64_t*>(&m->x), ts);
+                    st_release(reinterpret_cast<uint64_t*>(&m->y), ts);
+                }
+            order_key = ts;
+            seq_out = (uint32_t)sq;
+            return COMMIT;
+        }
+    }
+    for (uint32_t k = 0; k < kmax; ++k)
+        if (held >> k & 1) {
+            const uint32_t j = L.lig + k * L.G;
+            st_release(reinterpret_cast<uint64_t*>(&words[Work::rec(a, S.desc[j])].y), S.obs[j]);
+        }
+    crec = group_conflict(L, frec);
+    return ABORT;
+}
+
+// ---------------------------------------------------------------------------
 // DET
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool det_wait(const ExecArgs& a, uint64_t* m, bool is_write,
@@ -605,7 +753,7 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
         if (go || expired) {
             const ExecArgs& a = *A;
             unsigned long long order_key = 0;
-            uint32_t crec = NO_CC;
+            uint32_t crec = NO_CC, seq = 0;
             int outcome = GIVE_UP;
             if (go) {
                 ++attempts;
@@ -615,6 +763,9 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
                     outcome = tpl_attempt<Work>(a, L, S, t, first, nops, attempts, order_key, crec);
                 else if constexpr (SCHEME == GCC_TO)
                     outcome = to_attempt<Work>(a, L, S, t, first, nops, attempts, order_key, crec);
+                else if constexpr (SCHEME == GCC_TICTOC)
+                    outcome = tictoc_attempt<Work>(a, L, S, t, first, nops, attempts, order_key,
+                                                   seq, crec);
                 else
                     outcome = det_attempt<Work>(a, L, S, t, first, nops, order_key);
             } else if (L.lig == 0) {
@@ -651,6 +802,7 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
                     a.results[t] = gcc_txn_result{GCC_TXN_COMMITTED, attempts,
                                                   DENSE ? (uint64_t)order_key : ~0ull};
                     if (!DENSE) a.order_key[t] = order_key;
+                    if constexpr (SCHEME == GCC_TICTOC) a.seq[t] = seq;
                     ++c.commits;
                 }
             } else if (outcome == GIVE_UP) {

@@ -261,6 +261,26 @@ __global__ void dense_rank(const uint32_t* __restrict__ sk, const uint32_t* __re
     res[sv[p]].commit_order = p;
 }
 
+// TicToc's serial order, (timestamp, sequence number), by three stable 32-bit
+// sorts: sequence number, then the timestamp's low and high words.  Pass 0
+// keys each transaction by its sequence number; passes 1 and 2 re-key the
+// sorted order by a timestamp word.  Transactions that did not commit carry
+// all-ones keys and stay last.
+__global__ void tt_emit(const gcc_txn_result* __restrict__ res,
+                        const unsigned long long* __restrict__ okey,
+                        const uint32_t* __restrict__ seq, const uint32_t* __restrict__ sv,
+                        int pass, uint32_t n, uint32_t* __restrict__ keys,
+                        uint32_t* __restrict__ vals) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint32_t t = pass == 0 ? p : sv[p];
+    const bool c = res[t].status == GCC_TXN_COMMITTED;
+    uint32_t k = 0xffffffffu;
+    if (c) k = pass == 0 ? seq[t] : pass == 1 ? (uint32_t)okey[t] : (uint32_t)(okey[t] >> 32);
+    keys[p] = k;
+    vals[p] = t;
+}
+
 __global__ void batch_begin_kernel(BatchState* st, DbState* dbs, int scheme) {
     BatchState z{};
     z.ticket_base = scheme == GCC_TO ? dbs->to_clock : dbs->occ_clock;
@@ -328,6 +348,22 @@ cudaError_t densify_commit_order(const ExecArgs& a, SortScratch& s, cudaStream_t
     uint32_t *sk, *sv;
     cudaError_t e = radix_sort_pairs(s, n, 32, &sk, &sv, st);
     if (e != cudaSuccess) return e;
+    dense_rank<<<blocks_for(n, 256), 256, 0, st>>>(sk, sv, n, a.results);
+    return cudaGetLastError();
+}
+
+cudaError_t densify_tictoc(const ExecArgs& a, SortScratch& s, cudaStream_t st) {
+    const uint32_t n = a.n_txns;
+    if (n == 0) return cudaSuccess;
+    uint32_t *sk = nullptr, *sv = nullptr;
+    for (int pass = 0; pass < 3; ++pass) {
+        // the previous pass's sorted values feed the next pass's keys; when the
+        // sort left them in (k0, v0), tt_emit rewrites those in place by index
+        tt_emit<<<blocks_for(n, 256), 256, 0, st>>>(a.results, a.order_key, a.seq, sv, pass, n,
+                                                    s.k0, s.v0);
+        cudaError_t e = radix_sort_pairs(s, n, 32, &sk, &sv, st);
+        if (e != cudaSuccess) return e;
+    }
     dense_rank<<<blocks_for(n, 256), 256, 0, st>>>(sk, sv, n, a.results);
     return cudaGetLastError();
 }

@@ -24,7 +24,7 @@ inline uint64_t oe_rows(uint32_t col, uint64_t W, uint64_t cap) {
     return nd * cap * OE_LINES;                     // ol_*
 }
 
-enum MetaState { META_ZERO, META_OCC, META_TO, META_DET, META_UNKNOWN };
+enum MetaState { META_ZERO, META_OCC, META_TO, META_DET, META_TICTOC, META_UNKNOWN };
 
 // CUDA events bracketing the stages of one execution.
 struct StageRec {
@@ -57,6 +57,7 @@ using gcc::rt::META_ZERO;
 using gcc::rt::META_OCC;
 using gcc::rt::META_TO;
 using gcc::rt::META_DET;
+using gcc::rt::META_TICTOC;
 using gcc::rt::META_UNKNOWN;
 
 struct gcc_db {
