@@ -129,7 +129,7 @@ do_validate(const ExecArgs a, uint32_t* __restrict__ keys, uint32_t* __restrict_
                 for (uint32_t i = 0; i < j; ++i)
                     if (OeWork::rec(a, sdesc[wib][i]) == rj) bad = true;
             }
-            const Stage S{sdesc[wib], nullptr, nullptr, nullptr};
+            const Stage S{sdesc[wib], nullptr, nullptr, nullptr, nullptr};
             if (!OeWork::valid_shape(a, S, nops, tx.type)) bad = true;
         }
         bad = __any_sync(0xffffffffu, bad);

@@ -282,10 +282,12 @@ struct ExecArgs {
     uint32_t queue_after;       // aborts before a transaction uses the queues
 };
 
-// Shared-memory staging per op: descriptor, observed word, value read and
-// value to write: the read and write sets live in shared memory while the
-// transaction runs, so aborted attempts never touch the output arrays.
-constexpr uint32_t STAGE_BYTES_PER_OP = 8 + 8 + 16 + 16;
+
+// Shared-memory staging per op: descriptor, observed word, value read, value
+// to write and one more word (TicToc's rts): the read and write sets live in
+// shared memory while the transaction runs, so aborted attempts never touch
+// the output arrays.
+constexpr uint32_t STAGE_BYTES_PER_OP = 8 + 8 + 16 + 16 + 8;
 
 // ---------------------------------------------------------------------------
 // host-side launchers (one translation unit each)

@@ -63,6 +63,7 @@ struct Stage {
     uint64_t* obs;
     ulonglong2* oldv;
     ulonglong2* newv;
+    uint64_t* aux;           // TicToc: the record's rts as read, then as locked
 };
 
 struct Lane {
@@ -376,9 +377,11 @@ __device__ __forceinline__ uint64_t group_max64(const Lane& L, uint64_t v) {
 }
 
 // Read phase as OCC's, recording each record's wts and rts; the write set is
-// locked without waiting; the commit timestamp is computed, not drawn from a
-// clock: at least every record read's wts and one past every record written's
-// rts.  A record read whose observed rts already covers the timestamp needs
+// locked without waiting, each lock a 128-bit CAS that also fixes the rts it
+// locks at (when only the rts moved since the read, a reader extended it: the
+// lock is retried at the new rts); the commit timestamp is computed, not drawn
+// from a clock: at least every record read's wts and one past every record
+// written's rts.  A record read whose observed rts already covers the timestamp needs
 // no check; otherwise its rts is extended to the timestamp with a 128-bit CAS
 // that also proves the version unchanged and unlocked.  Writes publish
 // wts = rts = timestamp.  Two commits never tie on a timestamp when they
@@ -394,7 +397,7 @@ __device__ int tictoc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, 
     ulonglong2* words = reinterpret_cast<ulonglong2*>(a.meta);
     bool fail = false;
     uint32_t frec = NO_CC;
-    // read phase: (wts, value, rts); a read op keeps its rts in newv.x
+    // read phase: (wts, value, rts)
     for (uint32_t k = 0; k < kmax; ++k) {
         const uint32_t j = L.lig + k * L.G;
         if (j < nops) {
@@ -414,8 +417,8 @@ __device__ int tictoc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, 
                         const ulonglong2 v = Work::load(a, d);
                         S.obs[j] = y1;
                         S.oldv[j] = v;
+                        S.aux[j] = ld_relaxed(rts_word);
                         if (w) S.newv[j] = Work::compute(a, d, v, opd);
-                        else S.newv[j] = make_ulonglong2(ld_relaxed(rts_word), 0ull);
                         break;
                     }
                     if (tries >= a.read_retries) { fail = true; frec = r; break; }
@@ -434,9 +437,19 @@ __device__ int tictoc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, 
         const uint32_t j = L.lig + k * L.G;
         if (j < nops && Work::writes(S.desc[j])) {
             const uint32_t r = Work::rec(a, S.desc[j]);
-            uint64_t* wts_word = reinterpret_cast<uint64_t*>(&words[r].y);
             bool ok = !collapse_loser(a, r);
-            if (ok) ok = cas64_acquire(wts_word, S.obs[j], S.obs[j] | TT_LOCK) == S.obs[j];
+            if (ok) {
+                ulonglong2 expect = make_ulonglong2(S.aux[j], S.obs[j]);
+                ok = false;
+                for (uint32_t tries = 0; tries <= a.read_retries; ++tries) {
+                    const ulonglong2 o = cas128_acquire(words + r, expect,
+                                                        make_ulonglong2(expect.x, expect.y | TT_LOCK));
+                    if (o.x == expect.x && o.y == expect.y) { ok = true; break; }
+                    if (o.y != S.obs[j]) break;          // written or locked since
+                    expect.x = o.x;
+                }
+                if (ok) S.aux[j] = expect.x;             // rts under the lock
+            }
             if (ok) held |= 1ull << k; else { fail = true; frec = r; }
         }
         if (__any_sync(L.gmask, fail)) break;
@@ -444,16 +457,14 @@ __device__ int tictoc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, 
     fail = __any_sync(L.gmask, fail) || injected_abort(a, t, attempt);
     if (!fail) {
         // the timestamp: a locked record's rts no longer moves (extensions
-        // need it unlocked)
+        // need it unlocked), and the lock fixed it
         uint64_t c = 0;
         for (uint32_t k = 0; k < kmax; ++k) {
             const uint32_t j = L.lig + k * L.G;
             if (j < nops) {
                 const uint32_t r = Work::rec(a, S.desc[j]);
                 if (r == NO_CC) continue;
-                const uint64_t cand = Work::writes(S.desc[j])
-                    ? ld_relaxed(reinterpret_cast<uint64_t*>(&words[r].x)) + 1
-                    : S.obs[j];
+                const uint64_t cand = Work::writes(S.desc[j]) ? S.aux[j] + 1 : S.obs[j];
                 c = cand > c ? cand : c;
             }
         }
@@ -467,7 +478,7 @@ __device__ int tictoc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, 
             const uint32_t j = L.lig + k * L.G;
             if (j < nops && !Work::writes(S.desc[j])) {
                 const uint32_t r = Work::rec(a, S.desc[j]);
-                if (r == NO_CC || S.newv[j].x >= ts) continue;
+                if (r == NO_CC || S.aux[j] >= ts) continue;
                 ulonglong2* m = words + r;
                 bool ok = false;
                 for (uint32_t tries = 0; tries <= a.read_retries; ++tries) {
@@ -848,6 +859,7 @@ __device__ __forceinline__ void setup_lanes(uint32_t G, uint32_t M, Lane& L, Sta
     ulonglong2* w128 = reinterpret_cast<ulonglong2*>(w64 + 2 * (size_t)slots * M);
     S.oldv = w128 + (size_t)slot * M;
     S.newv = w128 + (size_t)slots * M + (size_t)slot * M;
+    S.aux = reinterpret_cast<uint64_t*>(w128 + 2 * (size_t)slots * M) + (size_t)slot * M;
 }
 
 // Warp-reduced counters into a batch's state: one atomic per warp and field.
