@@ -397,7 +397,10 @@ __device__ int tictoc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, 
     ulonglong2* words = reinterpret_cast<ulonglong2*>(a.meta);
     bool fail = false;
     uint32_t frec = NO_CC;
-    // read phase: (wts, value, rts)
+    // read phase: (wts, value, rts) of one version.  A read whose rts already
+    // covers the commit timestamp is not checked again, so the three must be
+    // one snapshot: wts is read again after the value and rts, and the read
+    // retried if a writer locked or published in between.
     for (uint32_t k = 0; k < kmax; ++k) {
         const uint32_t j = L.lig + k * L.G;
         if (j < nops) {
@@ -415,11 +418,15 @@ __device__ int tictoc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, 
                     const uint64_t y1 = ld_acquire(wts_word);
                     if (!(y1 & TT_LOCK)) {
                         const ulonglong2 v = Work::load(a, d);
-                        S.obs[j] = y1;
-                        S.oldv[j] = v;
-                        S.aux[j] = ld_relaxed(rts_word);
-                        if (w) S.newv[j] = Work::compute(a, d, v, opd);
-                        break;
+                        const uint64_t rts = ld_relaxed(rts_word);
+                        fence_acq_rel();
+                        if (ld_relaxed(wts_word) == y1) {
+                            S.obs[j] = y1;
+                            S.oldv[j] = v;
+                            S.aux[j] = rts;
+                            if (w) S.newv[j] = Work::compute(a, d, v, opd);
+                            break;
+                        }
                     }
                     if (tries >= a.read_retries) { fail = true; frec = r; break; }
                     __nanosleep(32);

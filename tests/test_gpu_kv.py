@@ -301,6 +301,25 @@ def test_ycsb_full_size(eng, theta):
             state = final
 
 
+def test_tictoc_hot_reads_replay(eng):
+    """TicToc skips re-checking a read whose read timestamp already covers the
+    commit timestamp, so every read must be a consistent (wts, value, rts)
+    snapshot: read-mostly batches on a few very hot records, several in a row,
+    replay exactly."""
+    nrec = 1 << 10
+    state = wl.kv_table_splitmix(31, nrec, 2)
+    with eng.Database("kv", n_records=nrec, n_fields=2, field_bytes=8, max_batch_txns=16384) as db:
+        db.load_kv(state)
+        for i in range(4):
+            batch = wl.kv_batch(32 + i, nrec=nrec, nfields=2, n_txns=16384, read_ratio=0.9,
+                                theta=0.99)
+            res, reads, stats = go(eng, db, "tictoc", batch, **HOT)
+            final = db.read_kv()
+            assert stats["committed"] == batch.n_txns, stats
+            check(state, final, batch, res, reads, "tictoc", stats)
+            state = final
+
+
 @pytest.mark.parametrize("scheme", SCHEMES)
 def test_hot_key_zipf_099(eng, scheme):
     """Zipf 0.99 over 2^16 records, 4,096 txns x 16 ops: the hottest record is
