@@ -167,6 +167,20 @@ def sector_bytes(batch) -> dict:
 CAPTURED_TRAFFIC = {("occ", 1 << 24, 1 << 20, 0.8, 0.5, 0, 0): 3.51e9 + 721.68e6}
 
 
+def replica_totals(dist, committed: float, elapsed: float, device=None):
+    """Whole-job totals over replicas (one independent database and batch per
+    rank): the committed transactions of all ranks and the slowest rank's
+    elapsed time.  Without a process group, the local values."""
+    if dist is None:
+        return committed, elapsed
+    import torch
+    c = torch.tensor([float(committed)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(c.item()), float(t.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -303,13 +317,9 @@ def run_ours(args, rank, world, dist):
 
     with ClockSampler(dev) as clocks:
         ms, hist, stats = timed(args.scheme, args.steps, args.warmup)
-        ms_max = ms
-        if dist is not None:
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_max = float(t.item())
         committed = stats["committed"]
-        value = committed * args.steps * world / (ms_max / 1000.0)
+        committed_all, ms_max = replica_totals(dist, committed * args.steps, ms, dev)
+        value = committed_all / (ms_max / 1000.0)
         kernel_ms = statistics.mean(h["kernel_ms"] for h in hist)
         launches = sum(h["kernel_launches"] for h in hist)
 
@@ -352,11 +362,8 @@ def run_ours(args, rank, world, dist):
                 committed_e2e += api_step()["committed"]
             barrier()
             dt = time.perf_counter() - t0
-            if dist is not None:
-                t = torch.tensor([dt], dtype=torch.float64, device=dev)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                dt = float(t.item())
-            e2e = {"value": committed_e2e * world / dt, "unit": "txn/s",
+            committed_e2e, dt = replica_totals(dist, committed_e2e, dt, dev)
+            e2e = {"value": committed_e2e / dt, "unit": "txn/s",
                    "h2d_bytes_per_step": batch.n_txns * 8 + batch.n_ops * 24,
                    "d2h_bytes_per_step": batch.n_txns * 16 + batch.n_ops * 16,
                    "steps": e2e_steps, "api": "gcc_txn_batch_submit + gcc_batch_wait"}
