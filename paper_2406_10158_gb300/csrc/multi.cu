@@ -26,7 +26,25 @@ struct MultiState {
     unsigned long long fetch;
     unsigned long long total;
     DbState clock;                 // shared OCC / TO clock of the launch
+    unsigned long long padded;     // fetch space: chunks rounded up to a power of two
+    unsigned int chunk_bits;       // log2 of the number of chunks in it
+    unsigned int pad;
 };
+
+// Transactions are handed out in chunks of FETCH_CHUNK consecutive ids, the
+// chunks in bit-reversed order over the fetch space, so that consecutive
+// fetches land far apart -- in different databases -- and every database's
+// batch advances at a rate proportional to its size.  Handed out database
+// after database instead, the batches' hot-record chains would run one after
+// the other, as they do in separate launches.
+constexpr uint32_t FETCH_CHUNK_BITS = 5;
+
+__device__ __forceinline__ unsigned long long interleaved_id(unsigned long long g, unsigned bits) {
+    const unsigned long long chunk = g >> FETCH_CHUNK_BITS;
+    const unsigned long long off = g & ((1ull << FETCH_CHUNK_BITS) - 1);
+    const unsigned long long rc = bits ? (__brevll(chunk) >> (64 - bits)) : 0ull;
+    return (rc << FETCH_CHUNK_BITS) | off;
+}
 
 __device__ __forceinline__ uint32_t find_batch(const uint32_t* prefix, uint32_t n, uint64_t g) {
     uint32_t lo = 0, hi = n;       // prefix[lo] <= g < prefix[hi]
@@ -58,13 +76,18 @@ struct MultiFetch {
         *c = Counters{};
     }
     __device__ __forceinline__ bool next(const Lane& L, uint32_t& t, const ExecArgs*& A) {
-        unsigned long long g = 0;
-        if (L.lig == 0) g = agg_ticket(&ms->fetch);
-        g = __shfl_sync(L.gmask, g, L.gbase);
-        if (g >= ms->total) return false;
-        const uint32_t i = find_batch(prefix, n, g);
+        unsigned long long id = 0;
+        for (;;) {                 // ids past the last transaction are skipped
+            unsigned long long g = 0;
+            if (L.lig == 0) g = agg_ticket(&ms->fetch);
+            g = __shfl_sync(L.gmask, g, L.gbase);
+            if (g >= ms->padded) return false;
+            id = interleaved_id(g, ms->chunk_bits);
+            if (id < ms->total) break;
+        }
+        const uint32_t i = find_batch(prefix, n, id);
         A = args + i;
-        t = (uint32_t)(g - prefix[i]);
+        t = (uint32_t)(id - prefix[i]);
         if (A != cur) {
             flush(L);
             cur = A;
@@ -417,6 +440,13 @@ gcc_status gcc_multi_plan_create(gcc_scheme scheme, const gcc_multi_batch* b, ui
     }
     gcc::MultiState ms{};
     ms.total = total;
+    {
+        const uint64_t chunks = (total + (1u << gcc::FETCH_CHUNK_BITS) - 1) >> gcc::FETCH_CHUNK_BITS;
+        unsigned bits = 0;
+        while ((1ull << bits) < chunks) ++bits;
+        ms.chunk_bits = bits;
+        ms.padded = (1ull << bits) << gcc::FETCH_CHUNK_BITS;
+    }
     if (cudaMemcpy(pl->d_args, args.data(), sizeof(gcc::ExecArgs) * n, cudaMemcpyHostToDevice) ||
         cudaMemcpy(pl->d_prefix, prefix.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice) ||
         cudaMemcpy(pl->d_own, own.data(), sizeof(gcc::DbState*) * n, cudaMemcpyHostToDevice) ||
