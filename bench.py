@@ -28,7 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "committed txns/s + abort rate on 1 GB300 vs plain launch; p99 commit latency"
-SCHEMES = ["occ", "2pl", "to", "tictoc", "det"]
+SCHEMES = ["occ", "2pl", "2pl_wd", "to", "tictoc", "det"]
 
 
 def parse_args(argv=None):

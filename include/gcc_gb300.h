@@ -50,8 +50,10 @@ typedef enum gcc_scheme {
     GCC_TO = 1,            /* basic timestamp ordering with a commit (dirty) bit */
     GCC_OCC = 2,           /* read-validate-write OCC with commit timestamps    */
     GCC_DET = 3,           /* deterministic conflict-ordered batch (GPUTx-like) */
-    GCC_TICTOC = 4         /* OCC with timestamps computed from per-record write
+    GCC_TICTOC = 4,        /* OCC with timestamps computed from per-record write
                               and read timestamps (TicToc, Table I) */
+    GCC_2PL_WAIT_DIE = 5   /* two-phase locking, an older transaction waits for a
+                              younger exclusive holder, a younger one aborts */
 } gcc_scheme;
 
 typedef enum gcc_schema {

@@ -257,7 +257,8 @@ gcc_status prepare_meta(gcc_db* db, gcc_scheme scheme, cudaStream_t st) {
     // the scheme cannot start from
     bool reset = false;
     switch (scheme) {
-        case GCC_NO_WAIT_2PL: reset = db->meta_state != META_ZERO; break;
+        case GCC_NO_WAIT_2PL:
+        case GCC_2PL_WAIT_DIE: reset = db->meta_state != META_ZERO; break;
         case GCC_OCC: reset = db->meta_state != META_ZERO && db->meta_state != META_OCC; break;
         case GCC_TO: reset = db->meta_state != META_ZERO && db->meta_state != META_TO; break;
         case GCC_DET: reset = false; break;    // per-record counters set by preprocessing
@@ -274,7 +275,8 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
                         const gcc_exec_params* params, gcc_txn_result* d_results,
                         gcc_operand* d_reads, cudaStream_t stream) {
     if (!db) return fail(GCC_ERR_INVALID, "null database");
-    if ((unsigned)scheme > GCC_TICTOC) return fail(GCC_ERR_INVALID, "unknown scheme %d", (int)scheme);
+    if ((unsigned)scheme > GCC_2PL_WAIT_DIE)
+        return fail(GCC_ERR_INVALID, "unknown scheme %d", (int)scheme);
     if (n_txns > db->d.max_batch_txns || n_ops > db->d.max_batch_ops)
         return fail(GCC_ERR_CAPACITY, "batch of %u txns / %llu ops exceeds the database maxima",
                     n_txns, (unsigned long long)n_ops);
@@ -419,7 +421,8 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     rec.used = true;
     db->n_stages++;
     switch (scheme) {
-        case GCC_NO_WAIT_2PL: db->meta_state = META_ZERO; break;
+        case GCC_NO_WAIT_2PL:
+        case GCC_2PL_WAIT_DIE: db->meta_state = META_ZERO; break;
         case GCC_OCC: db->meta_state = META_OCC; break;
         case GCC_TO: db->meta_state = META_TO; break;
         case GCC_DET: db->meta_state = META_DET; break;

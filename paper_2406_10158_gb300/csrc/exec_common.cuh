@@ -33,6 +33,9 @@
 //    timestamp, validate the read set, write and release with the new version
 //    (Sec. II-B, Sec. III-E.2 Silo: lock bit + 63-bit timestamp, no epochs,
 //    no-wait locking).  Commit order: the timestamp.
+//  * 2PL wait-die -- as NO_WAIT 2PL, but a transaction waits (bounded) for
+//    an exclusive lock held by a younger one, and dies otherwise (Sec. II-A,
+//    tpl_wd).  Commit order: the lock-point counter.
 //  * TicToc       -- OCC whose commit timestamp is computed from per-record
 //    write and read timestamps instead of a shared clock; a read stays valid
 //    by extending its record's read timestamp (Table I lists TicToc among the
@@ -214,10 +217,16 @@ __device__ int occ_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
 // ---------------------------------------------------------------------------
 // NO_WAIT 2PL
 // ---------------------------------------------------------------------------
-template <class Work>
+// With WAIT_DIE, a lock held exclusively by a younger transaction (larger id:
+// ids are fixed across restarts) is waited for, within a bound, instead of
+// aborting; a younger requester dies as in NO_WAIT.  Waits only ever go from
+// older to younger, so they cannot form a cycle.  A lock held shared is not
+// waited for (the word does not record the oldest shared holder).
+template <class Work, bool WAIT_DIE = false>
 __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint32_t t,
                            uint64_t first, uint32_t nops, uint32_t attempt,
                            unsigned long long& order_key, uint32_t& crec) {
+    const uint32_t wait_spins = WAIT_DIE ? 256u * (a.read_retries + 1u) : 0u;
     const uint32_t kmax = (nops + L.G - 1) / L.G;
     bool fail = false;
     uint32_t frec = NO_CC;
@@ -230,15 +239,34 @@ __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
             if (r != NO_CC) {
                 uint64_t* m = a.meta + r;
                 if (!Work::writes(d)) {
-                    for (uint32_t tries = 0;; ++tries) {
+                    uint32_t waited = 0;
+                    for (uint32_t tries = 0;;) {
                         const uint64_t w = ld_relaxed(m);
-                        if (w & TPL_X) { fail = true; frec = r; break; }
+                        if (w & TPL_X) {
+                            if (WAIT_DIE && t + 1 < (uint32_t)w && waited < wait_spins) {
+                                ++waited;
+                                __nanosleep(64);
+                                continue;
+                            }
+                            fail = true; frec = r; break;
+                        }
                         if (cas64_acquire(m, w, w + TPL_S_ONE) == w) { held |= 1ull << k; break; }
-                        if (tries >= a.read_retries) { fail = true; frec = r; break; }
+                        if (++tries > a.read_retries) { fail = true; frec = r; break; }
                     }
                 } else {
                     bool ok = !collapse_loser(a, r);
-                    if (ok) ok = cas64_acquire(m, 0ull, TPL_X | (uint64_t)(t + 1)) == 0ull;
+                    if (ok) {
+                        const uint64_t mine = TPL_X | (uint64_t)(t + 1);
+                        uint64_t cur = cas64_acquire(m, 0ull, mine);
+                        for (uint32_t waited = 0; WAIT_DIE && cur != 0ull && (cur & TPL_X) &&
+                                                  t + 1 < (uint32_t)cur && waited < wait_spins;
+                             ++waited) {
+                            __nanosleep(64);
+                            cur = ld_relaxed(m);
+                            if (cur == 0ull) cur = cas64_acquire(m, 0ull, mine);
+                        }
+                        ok = cur == 0ull;
+                    }
                     if (ok) held |= 1ull << k; else { fail = true; frec = r; }
                 }
             }
@@ -673,7 +701,8 @@ struct SingleFetch {
 template <int SCHEME, class Work, class Fetch>
 __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, uint64_t deadline,
                            Counters& c) {
-    constexpr bool DENSE = SCHEME == GCC_NO_WAIT_2PL || SCHEME == GCC_DET;
+    constexpr bool DENSE =
+        SCHEME == GCC_NO_WAIT_2PL || SCHEME == GCC_2PL_WAIT_DIE || SCHEME == GCC_DET;
     bool finished = false, has = false, served = false;
     uint32_t t = 0, nops = 0, attempts = 0;
     uint64_t wake = 0;            // global-timer time before which the group waits
@@ -781,6 +810,9 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
                     outcome = tpl_attempt<Work>(a, L, S, t, first, nops, attempts, order_key, crec);
                 else if constexpr (SCHEME == GCC_TO)
                     outcome = to_attempt<Work>(a, L, S, t, first, nops, attempts, order_key, crec);
+                else if constexpr (SCHEME == GCC_2PL_WAIT_DIE)
+                    outcome = tpl_attempt<Work, true>(a, L, S, t, first, nops, attempts, order_key,
+                                                      crec);
                 else if constexpr (SCHEME == GCC_TICTOC)
                     outcome = tictoc_attempt<Work>(a, L, S, t, first, nops, attempts, order_key,
                                                    seq, crec);

@@ -12,7 +12,7 @@ import oracle
 from paper_2406_10158_gb300 import workload as wl
 
 pytestmark = pytest.mark.gpu
-SCHEMES = ["occ", "2pl", "to", "tictoc", "det", "det-dataflow"]
+SCHEMES = ["occ", "2pl", "2pl_wd", "to", "tictoc", "det", "det-dataflow"]
 
 
 # Under heavy contention no-wait locking and timestamp ordering need retry
@@ -163,7 +163,7 @@ def test_edge_cases(eng, scheme):
             db.submit("det" if scheme.startswith("det") else scheme, big)
 
 
-@pytest.mark.parametrize("scheme", ["occ", "2pl", "to", "tictoc"])
+@pytest.mark.parametrize("scheme", ["occ", "2pl", "2pl_wd", "to", "tictoc"])
 def test_injected_aborts_and_backoff(eng, scheme):
     """Forced aborts at the commit point (30%) and randomized backoff exercise
     the retry path; the outcome still replays exactly."""
@@ -188,7 +188,7 @@ def test_attempt_budget_gives_up_cleanly(eng):
     with eng.Database("kv", n_records=1024, n_fields=8, field_bytes=8,
                       max_batch_txns=256) as db:
         db.load_kv(table)
-        for scheme in ("2pl", "occ", "to", "tictoc"):
+        for scheme in ("2pl", "2pl_wd", "occ", "to", "tictoc"):
             res, reads, stats = db.run(scheme, batch,
                                        eng.params(inject_abort_ppm=1000000, max_attempts=3))
             assert (res["status"] == oracle.ST_TIMEOUT).all(), scheme
@@ -199,7 +199,7 @@ def test_attempt_budget_gives_up_cleanly(eng):
         check(table, db.read_kv(), batch, res, reads, "2pl", stats)
 
 
-@pytest.mark.parametrize("scheme", ["occ", "2pl", "to", "tictoc"])
+@pytest.mark.parametrize("scheme", ["occ", "2pl", "2pl_wd", "to", "tictoc"])
 @pytest.mark.parametrize("policy", [dict(retry_queue=2), dict(queue_after=1),
                                     dict(queue_after=1, queue_width=4),
                                     dict(queue_after=3, queue_turn_ns=200)],
@@ -219,7 +219,7 @@ def test_retry_policies_replay(eng, scheme, policy):
     check(table, final, batch, res, reads, scheme, stats)
 
 
-@pytest.mark.parametrize("scheme", ["occ", "2pl", "to", "tictoc"])
+@pytest.mark.parametrize("scheme", ["occ", "2pl", "2pl_wd", "to", "tictoc"])
 def test_retry_queues_after_a_deadline(eng, scheme):
     """A hot batch cut off by a 1 ms kernel deadline while transactions wait in
     retry queues ends with TIMEOUT statuses and the deadline flag; what did
@@ -273,7 +273,8 @@ def test_schemes_share_one_database(eng):
                       max_batch_txns=4096) as db:
         db.load_kv(state)
         for i, scheme in enumerate(["occ", "occ", "2pl", "det", "to", "occ", "det-dataflow",
-                                    "tictoc", "tictoc", "2pl", "to", "tictoc", "det"]):
+                                    "tictoc", "tictoc", "2pl", "2pl_wd", "to", "tictoc",
+                                    "2pl_wd", "det"]):
             batch = wl.kv_batch(100 + i, nrec=nrec, nfields=4, n_txns=4096, theta=0.8)
             res, reads, stats = go(eng, db, scheme, batch)
             final = db.read_kv()

@@ -13,7 +13,7 @@ import oracle
 from paper_2406_10158_gb300 import workload as wl
 
 pytestmark = pytest.mark.gpu
-SCHEMES = ["occ", "2pl", "to", "tictoc", "det", "det-dataflow"]
+SCHEMES = ["occ", "2pl", "2pl_wd", "to", "tictoc", "det", "det-dataflow"]
 
 
 def scheme_params(eng, scheme, **kw):
@@ -96,5 +96,6 @@ def test_order_entry_rejects_malformed(eng):
 @pytest.mark.parametrize("W", [1, 8, 64])
 def test_order_entry_full_size(eng, W):
     """2^18 txns, 50/50 NewOrder/Payment, every scheme (the paper's TPC-C shape)."""
-    for scheme in ["occ", "2pl", "to", "tictoc", "det"] + (["det-dataflow"] if W > 1 else []):
+    for scheme in ["occ", "2pl", "2pl_wd", "to", "tictoc", "det"] + \
+            (["det-dataflow"] if W > 1 else []):
         run_and_check(eng, W, 1 << 18, scheme, seed=wl.SEEDS[2])
