@@ -178,7 +178,12 @@ typedef struct gcc_exec_params {
                                   (key-value: prefix sums; order-entry: one warp
                                   per record applies its ops in id order)
                                   [default]; 1 = run op by op in the execute
-                                  kernel, each op waiting for its predecessors */
+                                  kernel, each op waiting for its predecessors
+                                  (a read for the earlier writes, a write for
+                                  every earlier access); 2 = the same with every
+                                  access waiting for every earlier access to
+                                  its record, reads included (GaccO-style
+                                  hand-off, Sec. II-C) */
     uint32_t retry_queue;      /* 2PL/TO/OCC: 1 = an aborted transaction that
                                   conflicted on a record waits, holding nothing,
                                   in a FIFO queue for that record and re-attempts

@@ -249,6 +249,7 @@ gcc_status validate_params(const gcc_exec_params& p) {
         return fail(GCC_ERR_INVALID, "warps_per_block must be in 1..32");
     if (p.collapse > 2) return fail(GCC_ERR_INVALID, "collapse must be 0, 1 or 2");
     if (p.retry_queue > 2) return fail(GCC_ERR_INVALID, "retry_queue must be 0, 1 or 2");
+    if (p.det_dataflow > 2) return fail(GCC_ERR_INVALID, "det_dataflow must be 0, 1 or 2");
     return GCC_OK;
 }
 
@@ -329,6 +330,7 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     a.rq = (p.retry_queue == 2 || p.immediate_restart) ? nullptr : db->rq;
     a.rq_mask = gcc::RETRY_QUEUES - 1;
     a.queue_turn_ns = p.queue_turn_ns;
+    a.det_all = p.det_dataflow == 2 ? 1u : 0u;
     a.queue_width = p.queue_width;
     a.queue_after = queue_after_for(p, scheme);
 
@@ -380,7 +382,8 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     }
     if (scheme == GCC_DET && n_ops) {
         const int bits = std::max(1, kv ? bit_length(db->n_meta - 1) : bit_length(db->n_meta));
-        GCC_CK(gcc::det_prepare(a, db->sort, db->scan_tmp, bits, db->d.schema, st));
+        GCC_CK(gcc::det_prepare(a, db->sort, db->scan_tmp, bits, db->d.schema, st,
+                                p.det_dataflow == 2));
         launches += 1 + 3 * ((bits + 7) / 8) + 1 + 3 + 1;   // emit, sort, flags, scan, need
     }
     const int block = (int)p.warps_per_block * 32;

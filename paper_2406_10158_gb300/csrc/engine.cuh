@@ -260,6 +260,7 @@ struct ExecArgs {
     const uint32_t* need;         // DET: per-op wait threshold
     unsigned long long* order_key;// OCC/TO/TicToc: raw commit timestamp per txn
     uint32_t* seq;                // TicToc: commit sequence number per txn (ties)
+    uint32_t det_all;             // DET dataflow: every access waits for all earlier ones
     int order_key_uses_base;      // OCC: timestamps count from BatchState::ticket_base
     BatchState* st;
     DbState* dbs;
@@ -331,7 +332,7 @@ struct DetPrep {
     const uint32_t* op_cc_key;    // optional: concurrency-control record per op
 };
 cudaError_t det_prepare(const ExecArgs& a, SortScratch& s, uint32_t* scan_tmp, int key_bits,
-                        int schema, cudaStream_t st);
+                        int schema, cudaStream_t st, bool all_conflict = false);
 
 // Record `msg` as this thread's gcc_last_error() and return `s`.
 gcc_status set_error(gcc_status s, const char* msg);

@@ -593,7 +593,7 @@ __device__ int det_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
             }
             uint64_t* m = a.meta + r;
             const bool w = Work::writes(d);
-            if (!det_wait(a, m, w, a.need[first + j])) { fail = true; break; }
+            if (!det_wait(a, m, w || a.det_all, a.need[first + j])) { fail = true; break; }
             const ulonglong2 v = Work::load(a, d);
             S.oldv[j] = v;
             if (w) Work::store(a, d, Work::compute(a, d, v, a.operands[first + j]), first + j);
@@ -616,7 +616,7 @@ __device__ void det_skip(const ExecArgs& a, const Lane& L, uint64_t first, uint3
         const uint32_t rec = cc_record(d, Work::SCHEMA, a.n_warehouses, NO_CC);
         if (rec >= a.n_meta) continue;
         const bool w = kind_writes(op_kind(d));
-        if (det_wait(a, a.meta + rec, w, a.need[first + j]))
+        if (det_wait(a, a.meta + rec, w || a.det_all, a.need[first + j]))
             add64(a.meta + rec, w ? DET_WRITE_DONE : DET_READ_DONE);
     }
 }

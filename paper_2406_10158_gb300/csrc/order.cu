@@ -228,9 +228,11 @@ __global__ void det_flags(const uint64_t* __restrict__ ops, const uint32_t* __re
     flags[p] = kind_writes((uint32_t)(ops[sv[p]] >> 40) & 0xffu) ? 1u : 0u;
 }
 
+// need: a write (or, when every access conflicts, any op) waits for all
+// earlier ops on its record, a read for the earlier writes.
 __global__ void det_need(const uint64_t* __restrict__ ops, const uint32_t* __restrict__ sk,
                          const uint32_t* __restrict__ sv, const uint32_t* __restrict__ wpre,
-                         uint64_t n, uint32_t none, uint32_t* __restrict__ need,
+                         uint64_t n, uint32_t none, int all_conflict, uint32_t* __restrict__ need,
                          uint64_t* __restrict__ meta) {
     const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -238,7 +240,7 @@ __global__ void det_need(const uint64_t* __restrict__ ops, const uint32_t* __res
     if (key == none) return;
     const uint32_t op = sv[p];
     const bool w = kind_writes((uint32_t)(ops[op] >> 40) & 0xffu);
-    need[op] = w ? (uint32_t)p : wpre[p];
+    need[op] = (w || all_conflict) ? (uint32_t)p : wpre[p];
     if (p == 0 || sk[p - 1] != key) meta[key] = ((uint64_t)p << 32) | wpre[p];
 }
 
@@ -322,7 +324,7 @@ cudaError_t exclusive_scan_u32(uint32_t* d, size_t n, uint32_t* tmp, cudaStream_
 }
 
 cudaError_t det_prepare(const ExecArgs& a, SortScratch& s, uint32_t* scan_tmp, int key_bits,
-                        int schema, cudaStream_t st) {
+                        int schema, cudaStream_t st, bool all_conflict) {
     const uint64_t n = a.n_ops;
     if (n == 0) return cudaSuccess;
     const uint32_t none = (uint32_t)a.n_meta;   // sorts after every real record
@@ -335,7 +337,7 @@ cudaError_t det_prepare(const ExecArgs& a, SortScratch& s, uint32_t* scan_tmp, i
     det_flags<<<blocks_for(n, 256), 256, 0, st>>>(a.ops, sv, n, flags);
     e = exclusive_scan_u32(flags, n, scan_tmp, st);
     if (e != cudaSuccess) return e;
-    det_need<<<blocks_for(n, 256), 256, 0, st>>>(a.ops, sk, sv, flags, n, none,
+    det_need<<<blocks_for(n, 256), 256, 0, st>>>(a.ops, sk, sv, flags, n, none, all_conflict ? 1 : 0,
                                                  const_cast<uint32_t*>(a.need), a.meta);
     return cudaGetLastError();
 }

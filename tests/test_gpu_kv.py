@@ -12,7 +12,7 @@ import oracle
 from paper_2406_10158_gb300 import workload as wl
 
 pytestmark = pytest.mark.gpu
-SCHEMES = ["occ", "2pl", "2pl_wd", "to", "tictoc", "det", "det-dataflow"]
+SCHEMES = ["occ", "2pl", "2pl_wd", "to", "tictoc", "det", "det-dataflow", "det-gacco"]
 
 
 # Under heavy contention no-wait locking and timestamp ordering need retry
@@ -22,9 +22,12 @@ HOT = {"backoff_cap_ns": 16_000_000}
 
 def go(eng, db, scheme, batch, timeout_s=120, **kw):
     """Run a batch; "det-dataflow" is the deterministic scheme run op by op
-    (key-value batches otherwise take the prefix-sum evaluation)."""
+    (key-value batches otherwise take the prefix-sum evaluation), "det-gacco"
+    the same with every access to a record ordered, reads included."""
     if scheme == "det-dataflow":
         scheme, kw = "det", dict(kw, det_dataflow=1)
+    elif scheme == "det-gacco":
+        scheme, kw = "det", dict(kw, det_dataflow=2)
     return db.run(scheme, batch, eng.params(**kw) if kw else None, timeout_s=timeout_s)
 
 

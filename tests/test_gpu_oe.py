@@ -13,14 +13,17 @@ import oracle
 from paper_2406_10158_gb300 import workload as wl
 
 pytestmark = pytest.mark.gpu
-SCHEMES = ["occ", "2pl", "2pl_wd", "to", "tictoc", "det", "det-dataflow"]
+SCHEMES = ["occ", "2pl", "2pl_wd", "to", "tictoc", "det", "det-dataflow", "det-gacco"]
 
 
 def scheme_params(eng, scheme, **kw):
     """"det-dataflow" is the deterministic scheme run op by op in the execute
-    kernel (order-entry batches otherwise take the per-record pass)."""
+    kernel (order-entry batches otherwise take the per-record pass);
+    "det-gacco" the same with every access to a record ordered."""
     if scheme == "det-dataflow":
         scheme, kw = "det", dict(kw, det_dataflow=1)
+    elif scheme == "det-gacco":
+        scheme, kw = "det", dict(kw, det_dataflow=2)
     return scheme, (eng.params(**kw) if kw else None)
 
 
@@ -97,5 +100,5 @@ def test_order_entry_rejects_malformed(eng):
 def test_order_entry_full_size(eng, W):
     """2^18 txns, 50/50 NewOrder/Payment, every scheme (the paper's TPC-C shape)."""
     for scheme in ["occ", "2pl", "2pl_wd", "to", "tictoc", "det"] + \
-            (["det-dataflow"] if W > 1 else []):
+            (["det-dataflow", "det-gacco"] if W > 1 else []):
         run_and_check(eng, W, 1 << 18, scheme, seed=wl.SEEDS[2])
