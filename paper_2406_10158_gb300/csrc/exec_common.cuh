@@ -2,7 +2,7 @@
 //
 // A persistent kernel: a warp is split into lane groups of G lanes; each
 // group owns one transaction at a time, taken from a global counter in
-// transaction-id order (one atomic per warp).  Op j of a transaction is
+// transaction-id order (one atomic per warp and chunk of ids).  Op j of a transaction is
 // handled by lane j mod G, so a group issues up to G independent record
 // accesses at once, and group-wide decisions (abort, commit) are ballots over
 // the group.  Per-op state -- descriptor, observed control word, value read,
@@ -10,13 +10,17 @@
 // touches the output arrays.
 //
 // The groups of a warp advance in rounds.  In a round every group that holds
-// a transaction and is not backing off makes one attempt; an aborted
-// transaction sits out a random number of rounds that grows with its abort
-// count, and a warp with no group attempting sleeps for one round quantum.
-// Locks, dirty bits and write locks are only ever held inside an attempt, so
-// a sleeping warp never holds any.  A transaction restarts until it commits
-// (Sec. IV-A, "Experimental Procedure"), within an attempt budget and a
-// kernel deadline.
+// a transaction and is neither backing off nor waiting in a retry queue makes
+// one attempt.  An aborted transaction backs off until a global-timer
+// deadline drawn at random from a window that doubles with its abort count;
+// after queue_after aborts it then also waits its turn in a FIFO queue of the
+// record it conflicted on.  A warp with no group attempting sleeps until its
+// earliest deadline.  Locks, dirty bits and write locks are only ever held
+// inside an attempt, so a sleeping warp never holds any.  A transaction
+// restarts until it commits (Sec. IV-A, "Experimental Procedure"), within an
+// attempt budget and a kernel deadline.  Ordering between transactions rests
+// on acquire/release operations: lock acquisitions acquire, unlocks and
+// publishes release, OCC's commit timestamp is acquire-release.
 //
 // Schemes (Sec. II and Sec. III-E; control-word layouts in engine.cuh):
 //  * NO_WAIT 2PL  -- shared/exclusive lock per record taken before the access,
