@@ -164,7 +164,7 @@ def sector_bytes(batch) -> dict:
 # capture in profiles/occ_kv_exec_kernel_full_dram.md: valid only for that
 # kernel build and workload (OCC, default launch, 2^24 x 10 x 16 B, 2^20 txns,
 # Zipf 0.8, read ratio 0.5); None for anything else.
-CAPTURED_TRAFFIC = {}
+CAPTURED_TRAFFIC = {("occ", 1 << 24, 1 << 20, 0.8, 0.5, 0, 0): 3.51e9 + 722.34e6}
 
 
 def replica_totals(dist, committed: float, elapsed: float, device=None):
