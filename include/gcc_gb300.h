@@ -2,7 +2,7 @@
  * gcc_gb300.h -- C ABI of the GPU concurrency-control engine (sm_103a).
  *
  * The engine executes a batch of OLTP transactions concurrently on one GPU
- * under one of four concurrency-control schemes and returns, per transaction,
+ * under one of six concurrency-control schemes and returns, per transaction,
  * its commit status, its position in a commit order and the values it read.
  * It follows the paper's statement of the problem: transactions are run in
  * batches, one worker per transaction (Sec. III-B); read and write sets are
