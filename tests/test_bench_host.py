@@ -1,0 +1,57 @@
+"""Host arithmetic behind the benchmark's reported bounds."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_2406_10158_gb300 import workload as wl  # noqa: E402
+
+
+def _batch():
+    # txn 0: read key 3, add key 5; txn 1: add key 5, read key 7; txn 2: add key 5
+    return wl.kv_batch_from_lists([
+        [(3, 0, wl.OP_READ, 0, 0), (5, 1, wl.OP_ADD, 4, 0)],
+        [(5, 0, wl.OP_ADD, -2, 0), (7, 0, wl.OP_READ, 0, 0)],
+        [(5, 0, wl.OP_ADD, 9, 0)],
+    ], field_bytes=16)
+
+
+def test_algorithmic_bytes_count_each_op_once():
+    b = _batch()
+    alg = bench.algorithmic_bytes(b)
+    assert (alg["reads"], alg["writes"]) == (2, 3)
+    assert alg["bytes"] == 3 * 24 + 2 * 56 + 3 * 88
+
+
+def test_sector_bytes():
+    b = _batch()
+    s = bench.sector_bytes(b)
+    assert s["random"] == 5 * 64 + 3 * 64
+    assert s["stream"] == 3 * 24 + 5 * 8 + 3 * 16 + 5 * 16
+
+
+def test_hot_record_counts():
+    c = bench.hot_record_counts(_batch())
+    assert c == {"max_accesses": 3, "max_writes": 3}
+
+
+def test_hot_record_of_a_zipf_batch_matches_its_histogram():
+    b = wl.kv_batch(7, nrec=1 << 12, nfields=2, n_txns=2048, theta=0.9, read_ratio=0.5)
+    keys = b.ops["key"].astype(np.int64)
+    w = b.ops["kind"] == wl.OP_ADD
+    c = bench.hot_record_counts(b)
+    assert c["max_accesses"] == np.bincount(keys).max()
+    assert c["max_writes"] == np.bincount(keys[w]).max()
+    assert c["max_writes"] <= c["max_accesses"]
+
+
+def test_captured_traffic_only_for_the_captured_workload():
+    key = ("occ", 1 << 24, 1 << 20, 0.8, 0.5, 0, 0)
+    for k in bench.CAPTURED_TRAFFIC:
+        assert k == key
+    assert bench.CAPTURED_TRAFFIC.get(("occ", 1 << 24, 1 << 20, 0.6, 0.5, 0, 0)) is None
+    assert bench.CAPTURED_TRAFFIC.get(("2pl", 1 << 24, 1 << 20, 0.8, 0.5, 0, 0)) is None
