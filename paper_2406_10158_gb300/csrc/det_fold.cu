@@ -212,12 +212,17 @@ __device__ __forceinline__ ulonglong2 slot_plus(ulonglong2 v, Sum s) {
 }
 
 // Read values: initial slot value plus the exclusive prefix within the slot.
+// A slot whose accesses all lie in this tile also gets its final value here:
+// once the block's initial-value loads are done (the barrier), the slot's
+// last access writes initial + inclusive sum.  Slots whose accesses began in
+// an earlier tile are left to fold_finals, after every tile has loaded.
 template <int FB>
 __global__ void __launch_bounds__(FB_THREADS)
 fold_apply(const ExecArgs a, const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv,
            uint64_t n, uint32_t none, const Seg* __restrict__ tile_carry) {
     __shared__ Seg warp_tot[33];
-    const uint64_t base = (uint64_t)blockIdx.x * FB_TILE + (uint64_t)threadIdx.x * FB_ITEMS;
+    const uint64_t tile_base = (uint64_t)blockIdx.x * FB_TILE;
+    const uint64_t base = tile_base + (uint64_t)threadIdx.x * FB_ITEMS;
     Seg e[FB_ITEMS];
     Seg acc{0u, Sum{0, 0}};
 #pragma unroll
@@ -226,19 +231,39 @@ fold_apply(const ExecArgs a, const uint32_t* __restrict__ sk, const uint32_t* __
         acc = seg_combine(acc, e[i]);
     }
     Seg run = seg_combine(tile_carry[blockIdx.x], block_seg_exclusive(acc, warp_tot, nullptr));
+    const uint32_t before = tile_base > 0 ? sk[tile_base - 1] : none;   // key entering the tile
+    ulonglong2 fin[FB_ITEMS];
+    bool last[FB_ITEMS];
 #pragma unroll
     for (int i = 0; i < FB_ITEMS; ++i) {
         const uint64_t p = base + i;
         const Sum prefix = e[i].head ? Sum{0, 0} : run.v;
+        last[i] = false;
         if (p < n && sk[p] != none) {
+            const uint32_t k = sk[p];
             const uint32_t op = sv[p];
-            a.reads[op] = slot_plus<FB>(slot_load<FB>(a, sk[p]), prefix);
+            const ulonglong2 init = slot_load<FB>(a, k);
+            const ulonglong2 rd = slot_plus<FB>(init, prefix);
+            a.reads[op] = rd;
+            if ((p + 1 >= n || sk[p + 1] != k) && k != before) {
+                fin[i] = slot_plus<FB>(rd, e[i].v);
+                last[i] = fin[i].x != init.x || fin[i].y != init.y;   // skip unchanged slots
+            }
         }
         run = seg_combine(run, e[i]);
     }
+    __syncthreads();                      // every initial value of this tile has been read
+#pragma unroll
+    for (int i = 0; i < FB_ITEMS; ++i) {
+        if (!last[i]) continue;
+        uint8_t* dst = a.table + (uint64_t)sk[base + i] * FB;
+        if (FB == 16) *reinterpret_cast<ulonglong2*>(dst) = fin[i];
+        else *reinterpret_cast<uint64_t*>(dst) = fin[i].x;
+    }
 }
 
-// The last access of each slot installs the final value.
+// The last access of each slot whose accesses began in an earlier tile
+// installs the final value (the others were installed by fold_apply).
 template <int FB>
 __global__ void fold_finals(const ExecArgs a, const uint32_t* __restrict__ sk,
                             const uint32_t* __restrict__ sv, uint64_t n, uint32_t none) {
@@ -246,6 +271,8 @@ __global__ void fold_finals(const ExecArgs a, const uint32_t* __restrict__ sk,
     if (p >= n) return;
     const uint32_t k = sk[p];
     if (k == none || (p + 1 < n && sk[p + 1] == k)) return;
+    const uint64_t tile_base = p / FB_TILE * FB_TILE;
+    if (tile_base == 0 || sk[tile_base - 1] != k) return;     // installed by fold_apply
     const uint32_t op = sv[p];
     ulonglong2 v = a.reads[op];                   // initial value + every earlier delta
     if (d_kind(a.ops[op]) == GCC_OP_ADD) {
