@@ -49,6 +49,10 @@ struct Seg {
     uint32_t head;
     Sum v;
 };
+// Scratch of the fold: the tile carries, then one cached delta per op.
+size_t fold_carry_bytes(size_t n_ops) {
+    return (((n_ops + FB_TILE - 1) / FB_TILE + 1) * sizeof(Seg) + 255) & ~size_t(255);
+}
 // a followed by b
 __device__ __forceinline__ Seg seg_combine(Seg a, Seg b) {
     return Seg{a.head | b.head, b.head ? b.v : sum_add(a.v, b.v)};
@@ -170,15 +174,30 @@ __device__ __forceinline__ Seg element(const ExecArgs& a, const uint32_t* sk, co
     return Seg{head, v};
 }
 
+// The same element from the cache fold_tile_totals filled: the op's delta,
+// stored in sorted order, so the second pass streams it instead of gathering
+// the op and its operand again.
+__device__ __forceinline__ Seg cached_element(const uint32_t* sk, const Sum* cache, uint64_t p,
+                                              uint64_t n, uint32_t none) {
+    if (p >= n) return Seg{1u, Sum{0, 0}};
+    const uint32_t k = sk[p];
+    if (k == none) return Seg{1u, Sum{0, 0}};
+    return Seg{(p == 0 || sk[p - 1] != k) ? 1u : 0u, cache[p]};
+}
+
 template <int FB>
 __global__ void __launch_bounds__(FB_THREADS)
 fold_tile_totals(const ExecArgs a, const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv,
-                 uint64_t n, uint32_t none, Seg* __restrict__ tile_tot) {
+                 uint64_t n, uint32_t none, Seg* __restrict__ tile_tot, Sum* __restrict__ cache) {
     __shared__ Seg warp_tot[33];
     const uint64_t base = (uint64_t)blockIdx.x * FB_TILE + (uint64_t)threadIdx.x * FB_ITEMS;
     Seg acc{0u, Sum{0, 0}};
 #pragma unroll
-    for (int i = 0; i < FB_ITEMS; ++i) acc = seg_combine(acc, element<FB>(a, sk, sv, base + i, n, none));
+    for (int i = 0; i < FB_ITEMS; ++i) {
+        const Seg e = element<FB>(a, sk, sv, base + i, n, none);
+        if (base + i < n) cache[base + i] = e.v;
+        acc = seg_combine(acc, e);
+    }
     Seg total;
     block_seg_exclusive(acc, warp_tot, &total);
     if (threadIdx.x == 0) tile_tot[blockIdx.x] = total;
@@ -219,7 +238,8 @@ __device__ __forceinline__ ulonglong2 slot_plus(ulonglong2 v, Sum s) {
 template <int FB>
 __global__ void __launch_bounds__(FB_THREADS)
 fold_apply(const ExecArgs a, const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv,
-           uint64_t n, uint32_t none, const Seg* __restrict__ tile_carry) {
+           uint64_t n, uint32_t none, const Seg* __restrict__ tile_carry,
+           const Sum* __restrict__ cache) {
     __shared__ Seg warp_tot[33];
     const uint64_t tile_base = (uint64_t)blockIdx.x * FB_TILE;
     const uint64_t base = tile_base + (uint64_t)threadIdx.x * FB_ITEMS;
@@ -227,7 +247,7 @@ fold_apply(const ExecArgs a, const uint32_t* __restrict__ sk, const uint32_t* __
     Seg acc{0u, Sum{0, 0}};
 #pragma unroll
     for (int i = 0; i < FB_ITEMS; ++i) {
-        e[i] = element<FB>(a, sk, sv, base + i, n, none);
+        e[i] = cached_element(sk, cache, base + i, n, none);
         acc = seg_combine(acc, e[i]);
     }
     Seg run = seg_combine(tile_carry[blockIdx.x], block_seg_exclusive(acc, warp_tot, nullptr));
@@ -324,9 +344,10 @@ cudaError_t fold_run(const ExecArgs& a, SortScratch& s, uint32_t* scan_tmp, uint
         if (e != cudaSuccess) return e;
         const uint32_t ntiles = (uint32_t)((n + FB_TILE - 1) / FB_TILE);
         Seg* tiles = static_cast<Seg*>(seg_tmp);
-        fold_tile_totals<FB><<<ntiles, FB_THREADS, 0, st>>>(a, sk, sv, n, none, tiles);
+        Sum* cache = reinterpret_cast<Sum*>(static_cast<char*>(seg_tmp) + fold_carry_bytes(n));
+        fold_tile_totals<FB><<<ntiles, FB_THREADS, 0, st>>>(a, sk, sv, n, none, tiles, cache);
         fold_scan_tiles<<<1, FB_THREADS, 0, st>>>(tiles, ntiles);
-        fold_apply<FB><<<ntiles, FB_THREADS, 0, st>>>(a, sk, sv, n, none, tiles);
+        fold_apply<FB><<<ntiles, FB_THREADS, 0, st>>>(a, sk, sv, n, none, tiles, cache);
         fold_finals<FB><<<blocks_for(n, 256), 256, 0, st>>>(a, sk, sv, n, none);
     }
     if (a.n_txns) {
@@ -346,7 +367,7 @@ cudaError_t fold_run(const ExecArgs& a, SortScratch& s, uint32_t* scan_tmp, uint
 }  // namespace
 
 size_t fold_seg_bytes(size_t max_ops) {
-    return ((max_ops + FB_TILE - 1) / FB_TILE + 1) * sizeof(Seg);
+    return fold_carry_bytes(max_ops) + max_ops * sizeof(Sum);
 }
 
 cudaError_t det_fold_kv(const ExecArgs& a, uint32_t field_bytes, SortScratch& s,
