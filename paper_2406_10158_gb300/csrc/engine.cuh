@@ -140,12 +140,6 @@ __device__ __forceinline__ uint64_t add64_release(uint64_t* p, uint64_t v) {
 __device__ __forceinline__ uint64_t max64(uint64_t* p, uint64_t v) {
     return atomicMax(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
-__device__ __forceinline__ uint64_t and64(uint64_t* p, uint64_t v) {
-    return atomicAnd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
-}
-__device__ __forceinline__ uint64_t or64(uint64_t* p, uint64_t v) {
-    return atomicOr(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
-}
 __device__ __forceinline__ uint64_t add64(uint64_t* p, uint64_t v) {
     return atomicAdd(reinterpret_cast<unsigned long long*>(p), v);
 }
