@@ -91,6 +91,37 @@ __device__ __forceinline__ ulonglong2 apply(Record& r, uint64_t d, ulonglong2 op
     }
 }
 
+// Warehouse, district and customer ops only add to their record's columns
+// (Payment amounts, the order counter), so a run of them is a prefix sum: the
+// value an op reads is the record before the run plus the deltas of the ops
+// before it.  delta() gives an op's additions, read_of() what it reads from
+// the record as it stands before the op (the values apply() returns).
+__device__ __forceinline__ Record delta(uint64_t d, ulonglong2 opd) {
+    Record e{};
+    const uint64_t h = opd.x;
+    switch (op_kind(d)) {
+        case GCC_OE_W_PAY:
+        case GCC_OE_D_PAY: e.c[0] = h; break;
+        case GCC_OE_D_NEWORDER: e.c[2] = 1; break;
+        case GCC_OE_C_PAY:
+            e.c[0] = 0ull - h;
+            e.c[1] = h;
+            e.c[2] = 1;
+            break;
+        default: break;                              // reads
+    }
+    return e;
+}
+__device__ __forceinline__ ulonglong2 read_of(uint64_t d, const Record& b) {
+    switch (op_kind(d)) {
+        case GCC_OE_W_READ: return make_ulonglong2(b.c[1], 0ull);
+        case GCC_OE_D_NEWORDER: return make_ulonglong2(b.c[2], b.c[1]);
+        case GCC_OE_C_READ: return make_ulonglong2(b.c[3], b.c[0]);
+        case GCC_OE_C_PAY: return make_ulonglong2(b.c[0], b.c[2]);
+        default: return make_ulonglong2(b.c[0], 0ull);   // W_PAY, D_PAY
+    }
+}
+
 __global__ void do_fill_none(uint32_t* __restrict__ keys, uint64_t n, uint32_t none) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) keys[i] = none;
@@ -207,11 +238,18 @@ do_segments(const ExecArgs a, const uint32_t* __restrict__ sk, const uint32_t* _
         if (lane == 0)
             for (int c = 0; c < 4; ++c)
                 if (CLASS_COLS[cls][c] >= 0) r.c[c] = OeWork::get(a, CLASS_COLS[cls][c], row);
+        // additive classes: every lane holds the record and takes its own op
+        if (cls != STOCK)
+            for (int c = 0; c < 4; ++c) r.c[c] = __shfl_sync(0xffffffffu, r.c[c], 0);
         for (uint64_t base = start; base < end; base += 32) {
             const uint32_t cnt = (uint32_t)(end - base < 32 ? end - base : 32);
-            s_d[wib][lane] = d;
-            s_o[wib][lane] = o;
             const uint32_t vcur = v;
+            const uint64_t dcur = d;
+            const ulonglong2 ocur = o;
+            if (cls == STOCK) {
+                s_d[wib][lane] = d;
+                s_o[wib][lane] = o;
+            }
             __syncwarp();
             const uint64_t ni = base + 32 + lane;
             if (ni < end) {
@@ -219,11 +257,34 @@ do_segments(const ExecArgs a, const uint32_t* __restrict__ sk, const uint32_t* _
                 d = a.ops[v];
                 o = a.operands[v];
             }
-            if (lane == 0)
-                for (uint32_t k = 0; k < cnt; ++k) s_r[wib][k] = apply(r, s_d[wib][k], s_o[wib][k]);
-            __syncwarp();
-            if ((uint32_t)lane < cnt) a.reads[vcur] = s_r[wib][lane];
-            __syncwarp();
+            if (cls == STOCK) {
+                // the quantity rule is not a sum: lane 0 applies the ops in order
+                if (lane == 0)
+                    for (uint32_t k = 0; k < cnt; ++k)
+                        s_r[wib][k] = apply(r, s_d[wib][k], s_o[wib][k]);
+                __syncwarp();
+                if ((uint32_t)lane < cnt) a.reads[vcur] = s_r[wib][lane];
+                __syncwarp();
+            } else {
+                // a warp-wide inclusive scan of the column deltas
+                const Record e = (uint32_t)lane < cnt ? delta(dcur, ocur) : Record{};
+                Record inc = e;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const uint64_t y = __shfl_up_sync(0xffffffffu, inc.c[c], off);
+                        if (lane >= off) inc.c[c] += y;
+                    }
+                if ((uint32_t)lane < cnt) {
+                    Record before = r;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) before.c[c] += inc.c[c] - e.c[c];
+                    a.reads[vcur] = read_of(dcur, before);
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) r.c[c] += __shfl_sync(0xffffffffu, inc.c[c], cnt - 1);
+            }
         }
         if (lane == 0)
             for (int c = 0; c < 4; ++c)
