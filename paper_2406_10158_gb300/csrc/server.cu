@@ -54,10 +54,15 @@ struct Slot {
     SlotState state = FREE;
 };
 
+// A request waiting for a free slot.  Requests of a trace point into the
+// trace's arrays, which outlive the run; requests enqueued one by one own a
+// copy (the caller may reuse its buffers).
 struct Pending {
     gcc_txn txn;
-    std::vector<gcc_op> ops;
-    std::vector<gcc_operand> opd;
+    const gcc_op* ops;                 // ops and operands of the request: either
+    const gcc_operand* opd;            // the caller's, or own_ops / own_opd
+    std::vector<gcc_op> own_ops;
+    std::vector<gcc_operand> own_opd;
     uint64_t arrival, id;
 };
 
@@ -186,23 +191,39 @@ void append(Slot& sl, const gcc_txn& t, const gcc_op* ops, const gcc_operand* op
     sl.arrival.push_back(arrival);
 }
 
-// Admit one request; launches the forming batch when it is full.
+void park(Lane& l, const gcc_txn& t, const gcc_op* ops, const gcc_operand* opd,
+          uint64_t arrival, uint64_t id, bool borrowed) {
+    Pending p{t, ops, opd, {}, {}, arrival, id};
+    if (!borrowed) {
+        p.own_ops.assign(ops, ops + t.n_ops);
+        p.own_opd.assign(opd, opd + t.n_ops);
+        p.ops = nullptr;                           // resolved to the copies when used
+        p.opd = nullptr;
+    }
+    l.backlog.push_back(std::move(p));
+}
+
+const gcc_op* ops_of(const Pending& p) { return p.ops ? p.ops : p.own_ops.data(); }
+const gcc_operand* opd_of(const Pending& p) { return p.opd ? p.opd : p.own_opd.data(); }
+
+// Admit one request; launches the forming batch when it is full.  `borrowed`:
+// ops and opd stay valid until the request is appended to a batch.
 gcc_status admit(gcc_server* s, uint32_t li, const gcc_txn& t, const gcc_op* ops,
-                 const gcc_operand* opd, uint64_t arrival, uint64_t id) {
+                 const gcc_operand* opd, uint64_t arrival, uint64_t id, bool borrowed) {
     Lane& l = s->lanes[li];
-    uint64_t wbytes = 0;
-    for (uint32_t j = 0; j < t.n_ops; ++j) wbytes += writes(ops[j].kind) ? 16 : 0;
     if (!l.backlog.empty()) {                      // keep arrival order behind the backlog
-        l.backlog.push_back(Pending{t, {ops, ops + t.n_ops}, {opd, opd + t.n_ops}, arrival, id});
+        park(l, t, ops, opd, arrival, id, borrowed);
         return GCC_OK;
     }
+    uint64_t wbytes = 0;
+    for (uint32_t j = 0; j < t.n_ops; ++j) wbytes += writes(ops[j].kind) ? 16 : 0;
     if (l.forming >= 0 && !fits(l, l.slots[l.forming], t.n_ops, wbytes)) {
         gcc_status st = launch(s, l);
         if (st) return st;
     }
     if (l.forming < 0) l.forming = take_free(l);
     if (l.forming < 0) {                           // every slot in flight: wait in the backlog
-        l.backlog.push_back(Pending{t, {ops, ops + t.n_ops}, {opd, opd + t.n_ops}, arrival, id});
+        park(l, t, ops, opd, arrival, id, borrowed);
         return GCC_OK;
     }
     append(l.slots[l.forming], t, ops, opd, wbytes, arrival, id);
@@ -255,14 +276,15 @@ gcc_status pump(gcc_server* s, bool flush_all) {
             if (l.forming < 0) l.forming = take_free(l);
             if (l.forming < 0) break;
             Pending& p = l.backlog.front();
+            const gcc_op* pops = ops_of(p);
             uint64_t wbytes = 0;
-            for (const gcc_op& o : p.ops) wbytes += writes(o.kind) ? 16 : 0;
+            for (uint32_t j = 0; j < p.txn.n_ops; ++j) wbytes += writes(pops[j].kind) ? 16 : 0;
             if (!fits(l, l.slots[l.forming], p.txn.n_ops, wbytes)) {
                 gcc_status st = launch(s, l);
                 if (st) return st;
                 continue;
             }
-            append(l.slots[l.forming], p.txn, p.ops.data(), p.opd.data(), wbytes, p.arrival, p.id);
+            append(l.slots[l.forming], p.txn, pops, opd_of(p), wbytes, p.arrival, p.id);
             l.backlog.pop_front();
         }
         // a forming batch past its delay (or everything, when draining) launches
@@ -365,7 +387,7 @@ gcc_status gcc_server_enqueue(gcc_server* s, uint32_t lane, const gcc_txn* txn, 
     if (cudaSetDevice(s->device) != cudaSuccess) return fail(GCC_ERR_CUDA, "cannot select device");
     const uint64_t rid = s->next_id++;
     if (id) *id = rid;
-    return admit(s, lane, *txn, ops, operands, arrival_ns, rid);
+    return admit(s, lane, *txn, ops, operands, arrival_ns, rid, false);
 }
 
 gcc_status gcc_server_pump(gcc_server* s) {
@@ -426,8 +448,10 @@ gcc_status gcc_server_run_trace(gcc_server* s, uint32_t n, const uint32_t* lane_
     while (!st && s->trace_done < n) {
         const uint64_t now = now_ns() - t0;
         while (!st && next < n && arrival_offset_ns[next] <= now) {
+            // the trace's arrays outlive the run: a parked request points into them
             st = admit(s, lane_of[next], txns[next], ops + txns[next].first_op,
-                       operands + txns[next].first_op, t0 + arrival_offset_ns[next], next);
+                       operands + txns[next].first_op, t0 + arrival_offset_ns[next], next,
+                       true);
             ++next;
         }
         if (!st) st = pump(s, next == n);
