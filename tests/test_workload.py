@@ -67,3 +67,30 @@ def test_trace_interleave_and_select_round_trip():
     a = wl.poisson_arrivals(3, 10000, 1e6)
     assert (np.diff(a.astype(np.int64)) >= 0).all()
     assert abs(float(a[-1]) / 1e4 - 1000.0) < 50.0          # mean gap 1 us
+
+
+def test_batched_databases_in_range():
+    """64 databases: 2^16..2^22 records, 1,000..262,144 txns of 4..64 ops
+    (sizes drawn log-uniformly); here with small bounds to stay fast."""
+    spec = wl.batched_kv(9, n_db=6, rec_bits=(10, 12), txn_range=(100, 400), ops_range=(4, 64))
+    assert len(spec) == 6
+    for nrec, table, batch in spec:
+        assert nrec in (1 << 10, 1 << 11, 1 << 12)
+        assert table.shape == (8, nrec)
+        assert 100 <= batch.n_txns <= 400
+        n = batch.txns["n_ops"]
+        assert n.min() >= 4 and n.max() <= 64
+        assert (batch.ops["key"] < nrec).all()
+        # op ranges tile the op array in transaction-id order
+        first = batch.txns["first_op"].astype(np.int64)
+        assert first[0] == 0 and np.array_equal(first[1:], np.cumsum(n.astype(np.int64))[:-1])
+
+
+def test_poisson_arrivals_have_the_offered_rate():
+    rate, n = 1e6, 200_000
+    t = wl.poisson_arrivals(3, n, rate).astype(np.float64)
+    gaps = np.diff(t)
+    assert (gaps >= 0).all()
+    # exponential gaps: mean 1/rate, coefficient of variation 1
+    assert abs(gaps.mean() / (1e9 / rate) - 1.0) < 0.01
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.02
