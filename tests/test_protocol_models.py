@@ -1,0 +1,396 @@
+"""Step-level models of the commit protocols of OCC, NO_WAIT 2PL, 2PL
+wait-die, basic TO and TicToc (CPU only).
+
+Each transaction is a sequence of atomic shared-memory steps -- the loads,
+CASes, atomics and stores of the execute kernel's attempt, in the kernel's
+order -- and a seeded random scheduler interleaves the transactions of a
+small scenario.  For every schedule, the transactions that committed,
+replayed one after another in their reported commit order from the initial
+state, must reproduce every value they read and the final state: the
+definition of serializability the CUDA path is tested against, applied to the
+protocol itself.  Variants that were considered and rejected are modelled as
+negative controls, and the check must find a counterexample for each: OCC
+with the commit timestamp taken together with (not after) the write locks,
+2PL with the ticket taken before the lock point, basic TO reading without
+checking wts again after the value, and TicToc reading (wts, value, rts)
+without re-checking wts.
+"""
+import random
+
+import pytest
+
+LOCK = 1 << 62
+
+
+class Mem:
+    """Per-record shared state: value, a control word and (TicToc) an rts."""
+
+    def __init__(self, values):
+        self.val = list(values)
+        self.word = [0] * len(values)      # OCC: version | LOCK;  TicToc: wts | LOCK
+        self.rts = [0] * len(values)       # TicToc only
+        self.clock = 0                     # OCC commit timestamps
+        self.seq = 0                       # TicToc sequence numbers
+
+
+# ---------------------------------------------------------------------------
+# OCC: read phase, lock write set (no wait), timestamp, validate, write,
+# publish version = timestamp + 1.  Each `yield` ends one atomic step.
+# ---------------------------------------------------------------------------
+def occ_txn(m, ops, out, ticket_with_locks=False):
+    obs, reads, newv = {}, {}, {}
+    for (r, d) in ops:                                  # read phase
+        v1 = m.word[r]
+        yield
+        if v1 & LOCK:
+            return
+        x = m.val[r]
+        yield
+        obs[r], reads[r] = v1, x
+        if d is not None:
+            newv[r] = x + d
+    held = []
+    ts = None
+    if ticket_with_locks:                               # rejected variant
+        ts = m.clock
+        m.clock += 1
+        yield
+    for (r, d) in ops:                                  # lock the write set
+        if d is None:
+            continue
+        if m.word[r] != obs[r]:
+            for h in held:
+                m.word[h] = obs[h]
+            return
+        m.word[r] = obs[r] | LOCK
+        held.append(r)
+        yield
+    if ts is None:                                      # the design: after the locks
+        ts = m.clock
+        m.clock += 1
+        yield
+    for (r, d) in ops:                                  # validate the read set
+        if d is None:
+            ok = m.word[r] == obs[r]
+            yield
+            if not ok:
+                for h in held:
+                    m.word[h] = obs[h]
+                return
+    for r in held:                                      # write, then publish
+        m.val[r] = newv[r]
+        yield
+    for r in held:
+        m.word[r] = ts + 1
+        yield
+    out.append(((ts,), reads))
+
+
+# ---------------------------------------------------------------------------
+# TicToc: read (wts, value, rts) as a snapshot, lock writes by a CAS that
+# fixes the rts, timestamp = max(wts of reads, locked rts + 1 of writes),
+# sequence number, extend rts of reads not covered, write, publish [ts, ts].
+# ---------------------------------------------------------------------------
+def tictoc_txn(m, ops, out, recheck=True):
+    obs, rts_obs, reads, newv = {}, {}, {}, {}
+    for (r, d) in ops:                                  # read phase
+        y1 = m.word[r]
+        yield
+        if y1 & LOCK:
+            return
+        x = m.val[r]
+        yield
+        rt = m.rts[r]
+        yield
+        if recheck:
+            y2 = m.word[r]
+            yield
+            if y2 != y1:
+                return
+        obs[r], rts_obs[r], reads[r] = y1, rt, x
+        if d is not None:
+            newv[r] = x + d
+    held = []
+    for (r, d) in ops:                                  # lock the write set
+        if d is None:
+            continue
+        while True:                                     # 128-bit CAS on (rts, wts)
+            cur_w, cur_r = m.word[r], m.rts[r]
+            if cur_w == obs[r] and cur_r == rts_obs[r]:
+                m.word[r] = obs[r] | LOCK
+                yield
+                break
+            yield
+            if cur_w != obs[r]:
+                for h in held:
+                    m.word[h] = obs[h]
+                return
+            rts_obs[r] = cur_r                          # only rts moved: lock at it
+        held.append(r)
+    ts = 0
+    for (r, d) in ops:
+        ts = max(ts, rts_obs[r] + 1 if d is not None else obs[r])
+    sq = m.seq                                          # sequence number
+    m.seq += 1
+    yield
+    for (r, d) in ops:                                  # validate / extend reads
+        if d is not None or rts_obs[r] >= ts:
+            continue
+        while True:
+            cur_w, cur_r = m.word[r], m.rts[r]
+            yield
+            if cur_w != obs[r]:
+                for h in held:
+                    m.word[h] = obs[h]
+                return
+            if cur_r >= ts:
+                break
+            if m.word[r] == cur_w and m.rts[r] == cur_r:    # the CAS
+                m.rts[r] = ts
+                yield
+                break
+    for r in held:                                      # write, publish [ts, ts]
+        m.val[r] = newv[r]
+        yield
+        m.rts[r] = ts
+        yield
+        m.word[r] = ts
+        yield
+    out.append(((ts, sq), reads))
+
+
+# ---------------------------------------------------------------------------
+# 2PL: shared / exclusive lock words (NO_WAIT dies at once; wait-die lets an
+# older requester wait, a bounded number of steps, for a younger exclusive
+# holder), values read under the locks, the commit ticket taken while every
+# lock is held, writes, releases.
+# ---------------------------------------------------------------------------
+X = 1 << 40
+WAIT_STEPS = 6
+
+
+def tpl_txn(m, ops, out, tid, wait_die=False, ticket_first=False):
+    reads, newv, held = {}, {}, []
+    ts = None
+    if ticket_first:                                    # rejected variant
+        ts = m.clock
+        m.clock += 1
+        yield
+    fail = False
+    for (r, d) in ops:
+        waited = 0
+        while True:
+            w = m.word[r]
+            if d is None and not (w & X):
+                m.word[r] = w + 1                       # CAS w -> w + one share
+                break
+            if d is not None and w == 0:
+                m.word[r] = X | (tid + 1)               # CAS 0 -> exclusive
+                break
+            yield
+            if wait_die and (w & X) and tid + 1 < (w & (X - 1)) and waited < WAIT_STEPS:
+                waited += 1                             # older: wait for the younger holder
+                continue
+            fail = True
+            break
+        if fail:
+            break
+        held.append((r, d))
+        yield
+        x = m.val[r]
+        yield
+        reads[r] = x
+        if d is not None:
+            newv[r] = x + d
+    if not fail:
+        if ts is None:                                  # lock point
+            ts = m.clock
+            m.clock += 1
+            yield
+        for (r, d) in held:
+            if d is not None:
+                m.val[r] = newv[r]
+                yield
+    for (r, d) in held:                                 # release
+        m.word[r] = m.word[r] - 1 if d is None else 0
+        yield
+    if not fail:
+        out.append(((ts,), reads))
+
+
+# ---------------------------------------------------------------------------
+# basic TO: timestamp at the start; a read needs a clean wts <= ts, raises
+# rts to ts, loads the value and checks that wts did not move; a write needs
+# ts >= rts and ts >= wts and marks the word dirty with wts = ts by a 128-bit
+# CAS; writes, then wts published; an abort restores the saved wts.
+# ---------------------------------------------------------------------------
+DIRTY = 1 << 61
+
+
+def to_txn(m, ops, out, recheck=True):
+    ts = m.clock + 1
+    m.clock += 1
+    yield
+    reads, newv, saved = {}, {}, {}
+    fail = False
+    for (r, d) in ops:
+        if d is None:
+            for tries in range(3):
+                y1 = m.word[r]
+                yield
+                if (y1 & DIRTY) or ts < y1:
+                    fail = True
+                    break
+                m.rts[r] = max(m.rts[r], ts)            # atomic max
+                yield
+                x = m.val[r]
+                yield
+                if not recheck or m.word[r] == y1:
+                    reads[r] = x
+                    break
+                yield
+            else:
+                fail = True
+        else:
+            w_r, w_w = m.rts[r], m.word[r]              # one 128-bit load
+            yield
+            if (w_w & DIRTY) or ts < w_r or ts < w_w:
+                fail = True
+            elif m.rts[r] == w_r and m.word[r] == w_w:  # the CAS
+                m.word[r] = DIRTY | ts
+                saved[r] = w_w
+                yield
+                x = m.val[r]
+                yield
+                reads[r] = x
+                newv[r] = x + d
+            else:
+                fail = True
+        if fail:
+            break
+    if fail:
+        for r, w in saved.items():
+            m.word[r] = w
+            yield
+        return
+    for r in saved:
+        m.val[r] = newv[r]
+        yield
+    for r in saved:
+        m.word[r] = ts
+        yield
+    out.append(((ts,), reads))
+
+
+def run_schedule(make_txn, scenario, initial, seed):
+    """Interleave the scenario's transactions by a seeded random schedule;
+    returns (committed [(order key, reads, ops)], final values)."""
+    m = Mem(initial)
+    outs = [[] for _ in scenario]
+    gens = [make_txn(m, ops, outs[i], i) for i, ops in enumerate(scenario)]
+    live = list(range(len(gens)))
+    rng = random.Random(seed)
+    while live:
+        i = rng.choice(live)
+        try:
+            next(gens[i])
+        except StopIteration:
+            live.remove(i)
+    committed = []
+    for i, o in enumerate(outs):
+        if o:
+            key, reads = o[0]
+            committed.append((key, reads, scenario[i]))
+    return committed, m.val
+
+
+def serial_replay_ok(committed, initial, final):
+    """Committed transactions in order-key order, one after another, must read
+    what they read concurrently and leave the final values."""
+    val = list(initial)
+    for _, reads, ops in sorted(committed, key=lambda c: c[0]):
+        for (r, d) in ops:
+            if val[r] != reads[r]:
+                return False
+            if d is not None:
+                val[r] += d
+    return val == list(final)
+
+
+# scenarios: (record, delta) per op; delta None = read
+SCENARIOS = {
+    "write-skew": [[(0, None), (1, 5)], [(1, None), (0, 7)]],
+    "lost-update": [[(0, 1)], [(0, 2)], [(0, 4)]],
+    "read-then-overwrite": [[(0, None), (1, None)], [(0, 3)], [(1, 9), (0, 1)]],
+    "chains": [[(0, 1), (1, None)], [(1, 2), (2, None)], [(2, 3), (0, None)]],
+    "hot-reader": [[(0, None), (2, None)], [(0, 5), (1, None)], [(2, 4), (0, None)],
+                   [(0, 6)]],
+}
+
+
+def _count_violations(make_txn, scenario, n):
+    initial = [100, 200, 300]
+    bad = commits = 0
+    for seed in range(n):
+        committed, final = run_schedule(make_txn, scenario, initial, seed)
+        commits += len(committed)
+        if not serial_replay_ok(committed, initial, final):
+            bad += 1
+    return bad, commits
+
+
+MODELS = {
+    "occ": lambda m, ops, out, i: occ_txn(m, ops, out),
+    "2pl": lambda m, ops, out, i: tpl_txn(m, ops, out, i),
+    "2pl_wd": lambda m, ops, out, i: tpl_txn(m, ops, out, i, wait_die=True),
+    "to": lambda m, ops, out, i: to_txn(m, ops, out),
+    "tictoc": lambda m, ops, out, i: tictoc_txn(m, ops, out),
+}
+
+
+@pytest.mark.parametrize("scheme", sorted(MODELS))
+@pytest.mark.parametrize("name", sorted(SCENARIOS))
+def test_protocol_is_serializable(scheme, name):
+    bad, commits = _count_violations(MODELS[scheme], SCENARIOS[name], 4000)
+    assert bad == 0
+    assert commits > 0
+
+
+def test_occ_timestamp_taken_with_the_locks_is_not_serializable():
+    """Negative control: a writer's timestamp can precede a reader's
+    validation of the record the writer is locking."""
+    make = lambda m, ops, out, i: occ_txn(m, ops, out, ticket_with_locks=True)
+    bad = sum(_count_violations(make, SCENARIOS[n], 4000)[0] for n in SCENARIOS)
+    assert bad > 0
+
+
+def test_tictoc_without_the_snapshot_recheck_is_not_serializable():
+    """Negative control: wts read before a writer publishes, value and rts
+    after, and a read covered by that rts is never checked again."""
+    make = lambda m, ops, out, i: tictoc_txn(m, ops, out, recheck=False)
+    bad = sum(_count_violations(make, SCENARIOS[n], 4000)[0] for n in SCENARIOS)
+    assert bad > 0
+
+
+def test_2pl_ticket_before_the_lock_point_is_not_serializable():
+    """Negative control: a ticket taken before the locks orders a transaction
+    ahead of one whose write it then reads."""
+    make = lambda m, ops, out, i: tpl_txn(m, ops, out, i, ticket_first=True)
+    bad = sum(_count_violations(make, SCENARIOS[n], 4000)[0] for n in SCENARIOS)
+    assert bad > 0
+
+
+def test_to_read_without_the_wts_recheck_is_not_serializable():
+    """Negative control: a younger writer locks, writes and publishes between
+    the read's wts check and its value load."""
+    make = lambda m, ops, out, i: to_txn(m, ops, out, recheck=False)
+    bad = sum(_count_violations(make, SCENARIOS[n], 4000)[0] for n in SCENARIOS)
+    assert bad > 0
+
+
+def test_wait_die_lets_the_older_transaction_wait():
+    """The wait-die model commits at least as often as NO_WAIT on the
+    scenarios (waiting replaces some aborts) and stays serializable."""
+    nw = sum(_count_violations(MODELS["2pl"], SCENARIOS[n], 2000)[1] for n in SCENARIOS)
+    wd = sum(_count_violations(MODELS["2pl_wd"], SCENARIOS[n], 2000)[1] for n in SCENARIOS)
+    assert wd >= nw
