@@ -41,8 +41,12 @@ typedef enum gcc_status {
     GCC_ERR_TIMEOUT = 3,   /* host wait ran out, or a device budget was spent   */
     GCC_ERR_NOMEM = 4,     /* device or host allocation failed                  */
     GCC_ERR_DEVICE = 5,    /* the kernel reported an error flag (see stats)     */
-    GCC_ERR_CAPACITY = 6   /* batch larger than the database was created for    */
+    GCC_ERR_CAPACITY = 6   /* batch larger than the database was created for,
+                              or too many batches outstanding                   */
 } gcc_status;
+
+/* Batches submitted on one database and not yet released by gcc_batch_free. */
+#define GCC_MAX_OUTSTANDING_BATCHES 256u
 
 /* Concurrency-control schemes (Sec. II, Table I; Sec. III-E). */
 typedef enum gcc_scheme {
@@ -281,7 +285,8 @@ gcc_status gcc_default_params(gcc_exec_params *p);
  * pointers that must stay valid until gcc_batch_wait returns.  params may be
  * NULL (defaults).  stream: a cudaStream_t, or NULL for the database's own
  * stream.  Errors: GCC_ERR_INVALID (n_ops/op ranges inconsistent, bad
- * scheme), GCC_ERR_CAPACITY (beyond the create-time maxima), GCC_ERR_NOMEM,
+ * scheme), GCC_ERR_CAPACITY (beyond the create-time maxima, or
+ * GCC_MAX_OUTSTANDING_BATCHES batches not yet freed), GCC_ERR_NOMEM,
  * GCC_ERR_CUDA.  Per-transaction problems (bad keys, duplicates) are not
  * errors here: those transactions come back as GCC_TXN_INVALID. */
 gcc_status gcc_txn_batch_submit(gcc_db *db, gcc_scheme scheme, const gcc_txn *txns,

@@ -230,9 +230,10 @@ gcc_status create_impl(const gcc_db_desc* desc, gcc_db** out) {
     if (d.schema == GCC_SCHEMA_KV &&
         (s = dev_alloc(&db->fold_seg, gcc::fold_seg_bytes(d.max_batch_ops), "fold carries")))
         return bail(s);
-    db->n_h_states = 256;
+    db->n_h_states = GCC_MAX_OUTSTANDING_BATCHES;
     if (cudaMallocHost(&db->h_states, sizeof(gcc::BatchState) * db->n_h_states) != cudaSuccess)
         return bail(fail(GCC_ERR_NOMEM, "cannot allocate pinned batch states"));
+    for (uint32_t i = db->n_h_states; i > 0; --i) db->free_h_states.push_back(i - 1);
     for (auto& r : db->stages)
         for (auto& e : r.ev)
             if (cudaEventCreate(&e) != cudaSuccess)
@@ -588,6 +589,9 @@ gcc_status gcc_txn_batch_submit(gcc_db* db, gcc_scheme scheme, const gcc_txn* tx
     *out = nullptr;
     if (n_txns > db->d.max_batch_txns || n_ops > db->d.max_batch_ops)
         return fail(GCC_ERR_CAPACITY, "batch exceeds the database maxima");
+    if (db->free_h_states.empty())
+        return fail(GCC_ERR_CAPACITY, "%u batches outstanding on this database (free some first)",
+                    db->n_h_states);
     GCC_CK(cudaSetDevice(db->d.device));
     gcc_batch* b = new (std::nothrow) gcc_batch();
     if (!b) return fail(GCC_ERR_NOMEM, "host allocation failed");
@@ -596,7 +600,9 @@ gcc_status gcc_txn_batch_submit(gcc_db* db, gcc_scheme scheme, const gcc_txn* tx
     b->scheme = scheme;
     b->n_txns = n_txns;
     b->n_ops = n_ops;
-    b->h_state = &db->h_states[db->next_h_state++ % db->n_h_states];
+    b->h_slot = db->free_h_states.back();
+    db->free_h_states.pop_back();
+    b->h_state = &db->h_states[b->h_slot];
     auto bail = [&](gcc_status s) {
         gcc_batch_free(b);
         return s;
@@ -688,6 +694,7 @@ gcc_status gcc_batch_free(gcc_batch* b) {
     if (b->d_reads) cudaFreeAsync(b->d_reads, b->stream);
     if (b->ev_start) cudaEventDestroy(b->ev_start);
     if (b->ev_done) cudaEventDestroy(b->ev_done);
+    if (b->h_slot != UINT32_MAX) b->db->free_h_states.push_back(b->h_slot);
     delete b;
     return GCC_OK;
 }

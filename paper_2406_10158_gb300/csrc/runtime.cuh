@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 
 #include "engine.cuh"
 
@@ -89,9 +90,11 @@ struct gcc_db {
     cudaStream_t last_stream = nullptr;
     gcc_scheme last_scheme = GCC_OCC;
     uint64_t last_n_txns = 0;
-    // pinned copies of BatchState for submitted batches
+    // pinned copies of BatchState, one per outstanding batch (submitted, not
+    // yet freed); free_h_states lists the unused ones
     gcc::BatchState* h_states = nullptr;
-    uint32_t n_h_states = 0, next_h_state = 0;
+    uint32_t n_h_states = 0;
+    std::vector<uint32_t> free_h_states;
     // stage timing ring
     StageRec stages[STAGE_RING];
     uint64_t n_stages = 0;
@@ -107,6 +110,7 @@ struct gcc_batch {
     gcc_txn_result* d_results = nullptr;
     gcc_operand* d_reads = nullptr;
     gcc::BatchState* h_state = nullptr;   // pinned, filled at batch end
+    uint32_t h_slot = UINT32_MAX;         // its index in the database's h_states
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
     uint64_t stage_index = 0;             // its entry in the database's stage ring
 };

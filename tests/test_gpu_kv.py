@@ -166,6 +166,40 @@ def test_edge_cases(eng, scheme):
             db.submit("det" if scheme.startswith("det") else scheme, big)
 
 
+def test_outstanding_batch_limit(eng):
+    """Up to GCC_MAX_OUTSTANDING_BATCHES (256) submitted batches may be pending
+    on one database; one more is refused with GCC_ERR_CAPACITY until a batch
+    is freed.  Waited in reverse order, every batch still returns its own
+    reads and statistics: deterministic batches equal serial execution of the
+    batches in submission order, transaction by transaction."""
+    nrec = 256
+    state = wl.kv_table_splitmix(11, nrec, 2)
+    with eng.Database("kv", n_records=nrec, n_fields=2, field_bytes=8, max_ops_per_txn=4,
+                      max_batch_txns=16) as db:
+        db.load_kv(state)
+        batches = [wl.kv_batch(1000 + i, nrec=nrec, nfields=2, n_txns=16, ops_per_txn=4,
+                               theta=0.8) for i in range(258)]
+        handles = [db.submit("det", b) for b in batches[:256]]
+        with pytest.raises(eng.GCCError) as err:
+            db.submit("det", batches[256])
+        assert err.value.status == 6
+        expect = []
+        for b in batches[:256]:
+            state, reads = oracle.serial(state, b)
+            expect.append(reads)
+        # the oldest batch is released unread; its slot takes the next batch
+        handles[0].free()
+        handles[0] = db.submit("det", batches[256])
+        state, reads = oracle.serial(state, batches[256])
+        expect[0] = reads
+        for i in reversed(range(256)):
+            res, got, stats = handles[i].wait(120)
+            handles[i].free()
+            assert stats["committed"] == 16 and stats["device_error"] == 0, (i, stats)
+            assert np.array_equal(got, expect[i]), i
+        assert np.array_equal(db.read_kv(), state)
+
+
 @pytest.mark.parametrize("scheme", ["occ", "2pl", "2pl_wd", "to", "tictoc"])
 def test_injected_aborts_and_backoff(eng, scheme):
     """Forced aborts at the commit point (30%) and randomized backoff exercise
