@@ -408,7 +408,10 @@ gcc_status gcc_server_create(const gcc_server_lane *lanes, uint32_t n_lanes,
 
 /* Admit one transaction (host memory, copied) to `lane`.  Its ops start at
  * ops[0] (txn->first_op is ignored).  arrival_ns is its arrival time on the
- * host steady clock (see gcc_server_now_ns).  *request_id receives its id. */
+ * host steady clock (see gcc_server_now_ns).  *request_id receives its id.
+ * GCC_ERR_CAPACITY when txn->n_ops exceeds the database's max_ops_per_txn or
+ * the lane's batch op capacity (min(max_batch_txns * max_ops_per_txn,
+ * max_batch_ops)). */
 gcc_status gcc_server_enqueue(gcc_server *s, uint32_t lane, const gcc_txn *txn,
                               const gcc_op *ops, const gcc_operand *operands,
                               uint64_t arrival_ns, uint64_t *request_id);
@@ -427,8 +430,11 @@ gcc_status gcc_server_completions(gcc_server *s, gcc_completion *out, gcc_operan
 /* Open-loop replay of a request trace: request i (ops at
  * ops[txns[i].first_op ..]) arrives at start + arrival_offset_ns[i] for lane
  * lane_of[i]; the loop admits arrivals, launches and collects batches until
- * every request has completed.  out[i] and reads_out[txns[i].first_op ..]
- * receive the outcome of request i. */
+ * every request has completed.  Requests are admitted in index order, so
+ * arrival_offset_ns should be nondecreasing.  out[i] and
+ * reads_out[txns[i].first_op ..] receive the outcome of request i.
+ * GCC_ERR_INVALID (nothing run) for a bad lane or a request too large for its
+ * lane, as in gcc_server_enqueue. */
 gcc_status gcc_server_run_trace(gcc_server *s, uint32_t n, const uint32_t *lane_of,
                                 const gcc_txn *txns, const gcc_op *ops,
                                 const gcc_operand *operands, const uint64_t *arrival_offset_ns,

@@ -171,6 +171,13 @@ int take_free(Lane& l) {
     return -1;
 }
 
+// A request fits an empty batch of the lane: no more ops than a transaction
+// of the database may have, nor than a batch holds (max_batch_ops may be the
+// smaller).  Admission relies on it: every request fits a fresh slot.
+bool op_count_fits(const Lane& l, uint32_t nops) {
+    return nops <= l.cfg.db->d.max_ops_per_txn && nops <= l.ops_cap;
+}
+
 // Append to the forming slot; false when it must launch first.
 bool fits(const Lane& l, const Slot& sl, uint32_t nops, uint64_t wbytes) {
     return sl.n_txns < l.cfg.max_batch_txns && sl.n_ops + nops <= l.ops_cap &&
@@ -382,8 +389,8 @@ gcc_status gcc_server_enqueue(gcc_server* s, uint32_t lane, const gcc_txn* txn, 
                               const gcc_operand* operands, uint64_t arrival_ns, uint64_t* id) {
     if (!s || !txn || (txn->n_ops && (!ops || !operands)) || lane >= s->lanes.size())
         return fail(GCC_ERR_INVALID, "bad argument");
-    if (txn->n_ops > s->lanes[lane].cfg.db->d.max_ops_per_txn)
-        return fail(GCC_ERR_CAPACITY, "transaction has more ops than the database allows");
+    if (!op_count_fits(s->lanes[lane], txn->n_ops))
+        return fail(GCC_ERR_CAPACITY, "transaction has more ops than the lane's batches hold");
     if (cudaSetDevice(s->device) != cudaSuccess) return fail(GCC_ERR_CUDA, "cannot select device");
     const uint64_t rid = s->next_id++;
     if (id) *id = rid;
@@ -434,8 +441,7 @@ gcc_status gcc_server_run_trace(gcc_server* s, uint32_t n, const uint32_t* lane_
         return fail(GCC_ERR_INVALID, "bad argument");
     if (!idle(s) || !s->done.empty()) return fail(GCC_ERR_INVALID, "server is busy");
     for (uint32_t i = 0; i < n; ++i)
-        if (lane_of[i] >= s->lanes.size() ||
-            txns[i].n_ops > s->lanes[lane_of[i]].cfg.db->d.max_ops_per_txn)
+        if (lane_of[i] >= s->lanes.size() || !op_count_fits(s->lanes[lane_of[i]], txns[i].n_ops))
             return fail(GCC_ERR_INVALID, "request %u: bad lane or too many ops", i);
     if (cudaSetDevice(s->device) != cudaSuccess) return fail(GCC_ERR_CUDA, "cannot select device");
     s->trace_out = out;

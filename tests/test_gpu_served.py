@@ -113,3 +113,35 @@ def test_served_same_alone_and_in_the_mix(eng, scheme):
     # and both equal the serial execution of the requests
     ref_final, ref_reads = oracle.serial(table, s0)
     assert np.array_equal(ref_final, f0) and np.array_equal(ref_reads, r0)
+
+
+def test_server_rejects_requests_larger_than_a_batch(eng):
+    """A database whose batches hold fewer ops than a transaction may have:
+    a request that no batch of its lane can hold is refused on the host
+    (enqueue: capacity; trace: invalid, nothing run); one that fits is served."""
+    table = wl.kv_table_splitmix(41, 64, 2)
+    big = wl.kv_batch_from_lists([[(1, 0, 1, 5, 0), (2, 0, 0, 0, 0), (3, 1, 1, 9, 0)]])
+    small = wl.kv_batch_from_lists([[(4, 0, 1, 7, 0), (5, 1, 0, 0, 0)]])
+    with eng.Database("kv", n_records=64, n_fields=2, field_bytes=8, max_ops_per_txn=4,
+                      max_batch_txns=8, max_batch_ops=2) as db:
+        db.load_kv(table)
+        srv = eng.Server([(db, "occ", 8, 0, 30_000, 2)])
+        try:
+            with pytest.raises(eng.GCCError) as err:
+                srv.enqueue(0, big.txns[:1], big.ops, big.operands.astype(np.uint64),
+                            srv.now_ns())
+            assert err.value.status == 6
+            with pytest.raises(eng.GCCError) as err:
+                srv.run_trace(np.zeros(1, dtype=np.uint32), big, np.zeros(1, dtype=np.uint64))
+            assert err.value.status == 1
+            srv.enqueue(0, small.txns[:1], small.ops, small.operands.astype(np.uint64),
+                        srv.now_ns())
+            srv.drain()
+            comp, reads = srv.completions()
+        finally:
+            srv.close()
+        final = db.read_kv()
+    assert comp.size == 1 and comp["status"][0] == oracle.ST_COMMITTED
+    assert int(reads[0, 0]) == int(table[0, 4]) and int(reads[1, 0]) == int(table[1, 5])
+    assert int(final[0, 4]) == (int(table[0, 4]) + 7) % (1 << 64)
+    assert np.array_equal(np.delete(final.ravel(), 4), np.delete(table.ravel(), 4))
