@@ -394,3 +394,61 @@ def test_wait_die_lets_the_older_transaction_wait():
     nw = sum(_count_violations(MODELS["2pl"], SCENARIOS[n], 2000)[1] for n in SCENARIOS)
     wd = sum(_count_violations(MODELS["2pl_wd"], SCENARIOS[n], 2000)[1] for n in SCENARIOS)
     assert wd >= nw
+
+
+# ---------------------------------------------------------------------------
+# Retry queues: a queue word holds (tickets taken, tickets finished).  A
+# transaction takes a ticket k (the taken count before it) and is admitted
+# once k - finished, as a signed distance, is below the queue width; its
+# attempt then ends and counts one ticket finished.  With a width above one,
+# later tickets can finish first, so the distance of a ticket that was asleep
+# can be negative.
+# ---------------------------------------------------------------------------
+def run_queue(n, width, seed, signed=True, max_steps=20000):
+    """Random interleaving of n transactions through one queue; returns
+    (all served, largest number of admitted-and-unfinished tickets)."""
+    rng = random.Random(seed)
+    taken = finished = 0
+    state = ["new"] * n
+    ticket = [0] * n
+    left = [0] * n
+    running = peak = 0
+    for _ in range(max_steps):
+        live = [i for i in range(n) if state[i] != "done"]
+        if not live:
+            return True, peak
+        i = rng.choice(live)
+        if state[i] == "new":
+            ticket[i] = taken
+            taken += 1
+            state[i] = "wait"
+        if state[i] == "wait":
+            d = (ticket[i] - finished) & 0xFFFFFFFF
+            ahead = d - (1 << 32) if (signed and d >= 1 << 31) else d
+            if ahead < width:
+                state[i] = "run"
+                left[i] = rng.randint(1, 4)
+                running += 1
+                peak = max(peak, running)
+        elif state[i] == "run":
+            left[i] -= 1
+            if left[i] == 0:
+                finished += 1
+                running -= 1
+                state[i] = "done"
+    return False, peak
+
+
+@pytest.mark.parametrize("width", [1, 2, 4])
+def test_retry_queue_admits_at_most_width_and_serves_everyone(width):
+    for seed in range(300):
+        served, peak = run_queue(24, width, seed)
+        assert served, seed
+        assert peak <= width
+
+
+def test_retry_queue_with_an_unsigned_distance_strands_tickets():
+    """Negative control: read as unsigned, a negative distance looks huge and
+    the sleeping ticket is never admitted."""
+    stuck = sum(not run_queue(24, 4, seed, signed=False)[0] for seed in range(300))
+    assert stuck > 0
