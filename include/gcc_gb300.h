@@ -181,7 +181,10 @@ typedef struct gcc_exec_params {
                                   pass over the batch's accesses sorted by record
                                   (key-value: prefix sums; order-entry: one warp
                                   per record applies its ops in id order)
-                                  [default]; 1 = run op by op in the execute
+                                  [default; key-value needs n_records *
+                                  n_fields below 2^32, else the batch is
+                                  refused with GCC_ERR_CAPACITY]; 1 = run op
+                                  by op in the execute
                                   kernel, each op waiting for its predecessors
                                   (a read for the earlier writes, a write for
                                   every earlier access); 2 = the same with every

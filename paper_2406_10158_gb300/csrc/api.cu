@@ -287,6 +287,13 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     gcc_exec_params p = merged(params);
     gcc_status s = validate_params(p);
     if (s) return s;
+    // the prefix-sum evaluation sorts 32-bit slot ids, one id past the last
+    // slot marking invalid transactions' accesses
+    if (scheme == GCC_DET && db->d.schema == GCC_SCHEMA_KV && !p.det_dataflow &&
+        (uint64_t)db->d.n_fields * db->d.n_records >= (1ull << 32))
+        return fail(GCC_ERR_CAPACITY,
+                    "deterministic key-value batches by prefix sums need n_records * n_fields "
+                    "below 2^32 (det_dataflow = 1 has no such limit)");
     GCC_CK(cudaSetDevice(db->d.device));
     cudaStream_t st = stream ? stream : db->stream;
     StageRec& rec = db->stages[db->n_stages % STAGE_RING];
