@@ -242,7 +242,9 @@ typedef struct gcc_stage_times {
 /* device_error bits */
 #define GCC_DEVERR_WAIT_BUDGET   0x1u   /* a deterministic wait ran out        */
 #define GCC_DEVERR_DEADLINE      0x2u   /* deadline_ns passed                  */
-#define GCC_DEVERR_TS_OVERFLOW   0x4u   /* timestamp ordering ran past 2^31-1  */
+#define GCC_DEVERR_TS_OVERFLOW   0x4u   /* OCC/TO: the batch used 2^32-1 or
+                                           more timestamps; its commit order
+                                           is not valid                       */
 #define GCC_DEVERR_ATTEMPTS      0x8u   /* a transaction hit max_attempts      */
 #define GCC_DEVERR_INVALID       0x10u  /* a transaction was malformed         */
 #define GCC_DEVERR_INSERT        0x20u  /* an order insert had no free slot    */

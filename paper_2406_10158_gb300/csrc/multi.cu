@@ -161,9 +161,14 @@ __global__ void multi_rank_keys(const ExecArgs* __restrict__ args, const uint32_
     const uint32_t i = find_batch(prefix, n, g);
     const ExecArgs& a = args[i];
     const uint32_t t = (uint32_t)(g - prefix[i]);
-    const unsigned long long base = a.st->ticket_base;
-    keys[g] = a.results[t].status == GCC_TXN_COMMITTED ? (uint32_t)(a.order_key[t] - base)
-                                                       : 0xffffffffu;
+    uint32_t k = 0xffffffffu;
+    if (a.results[t].status == GCC_TXN_COMMITTED) {
+        // a 32-bit offset from the plan's starting clock, as in the plain path
+        const unsigned long long d = a.order_key[t] - a.st->ticket_base;
+        if (d >= 0xffffffffull) atomicOr(&a.st->error, GCC_DEVERR_TS_OVERFLOW);
+        k = (uint32_t)d;
+    }
+    keys[g] = k;
     vals[g] = (uint32_t)g;
 }
 

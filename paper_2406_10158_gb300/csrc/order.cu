@@ -245,14 +245,23 @@ __global__ void det_need(const uint64_t* __restrict__ ops, const uint32_t* __res
 }
 
 // --- dense commit ranks -------------------------------------------------------
+// Sort keys are 32-bit offsets from the batch's starting clock, all-ones
+// marking transactions that did not commit; a batch that used more
+// timestamps than that reports GCC_DEVERR_TS_OVERFLOW.
 __global__ void dense_emit(const gcc_txn_result* __restrict__ res,
                            const unsigned long long* __restrict__ okey,
-                           const BatchState* __restrict__ st, int use_base, uint32_t n,
+                           BatchState* __restrict__ st, int use_base, uint32_t n,
                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const unsigned long long base = use_base ? st->ticket_base : 0ull;
-    keys[t] = res[t].status == GCC_TXN_COMMITTED ? (uint32_t)(okey[t] - base) : 0xffffffffu;
+    uint32_t k = 0xffffffffu;
+    if (res[t].status == GCC_TXN_COMMITTED) {
+        const unsigned long long d = okey[t] - base;
+        if (d >= 0xffffffffull) atomicOr(&st->error, GCC_DEVERR_TS_OVERFLOW);
+        k = (uint32_t)d;
+    }
+    keys[t] = k;
     vals[t] = t;
 }
 
