@@ -452,3 +452,135 @@ def test_retry_queue_with_an_unsigned_distance_strands_tickets():
     the sleeping ticket is never admitted."""
     stuck = sum(not run_queue(24, 4, seed, signed=False)[0] for seed in range(300))
     assert stuck > 0
+
+
+# ---------------------------------------------------------------------------
+# Multi-version TO (the TO-based MVCC of Sec. III-E, "MVCC"; a design for a
+# device implementation, checked here before it is built).  Versions are
+# immutable once made.  Each record has one atomically updated head word
+# (wts of its newest committed version, that version's rts, the timestamp of
+# a pending writer or 0).  Writes happen only at the head: a writer with
+# timestamp ts needs no pending writer, wts < ts and rts <= ts, and installs
+# itself as the pending writer by a CAS; at commit it creates its version and
+# publishes (ts, ts, 0).  A read with timestamp ts aborts if a writer older
+# than ts is pending; if the head is older than ts it raises the head's rts
+# to ts by a CAS that keeps the rest of the word; otherwise it reads the
+# newest version older than ts, which no later write can displace (writes go
+# above the head only).  Serial order: the timestamps.
+# ---------------------------------------------------------------------------
+class MVMem:
+    def __init__(self, values):
+        self.head = [(0, 0, 0)] * len(values)           # (wts, rts, pending ts)
+        self.versions = [{0: v} for v in values]        # wts -> value, immutable
+        self.clock = 0
+
+
+def mvto_txn(m, ops, out, raise_rts=True, check_rts=True):
+    ts = m.clock + 1
+    m.clock += 1
+    yield
+    reads, newv, pending = {}, {}, []
+    fail = False
+    for (r, d) in ops:
+        for _ in range(3):                              # CAS retries
+            w, rt, pend = m.head[r]                     # one 16-byte load
+            yield
+            if d is None:
+                if pend and pend < ts:
+                    fail = True
+                    break
+                if w < ts:
+                    if raise_rts:
+                        if m.head[r] != (w, rt, pend):  # the CAS
+                            yield
+                            continue
+                        m.head[r] = (w, max(rt, ts), pend)
+                        yield
+                    reads[r] = m.versions[r][w]
+                else:
+                    older = max(k for k in m.versions[r] if k < ts)
+                    reads[r] = m.versions[r][older]
+                yield
+                break
+            if pend or w >= ts or (check_rts and rt > ts):
+                fail = True
+                break
+            if m.head[r] != (w, rt, pend):              # the CAS
+                yield
+                continue
+            m.head[r] = (w, rt, ts)
+            pending.append(r)
+            yield
+            reads[r] = m.versions[r][w]
+            newv[r] = reads[r] + d
+            yield
+            break
+        else:
+            fail = True
+        if fail:
+            break
+    if fail:
+        for r in pending:                               # withdraw, keeping rts raises
+            w, rt, _ = m.head[r]
+            m.head[r] = (w, rt, 0)
+            yield
+        return
+    for r in pending:
+        m.versions[r][ts] = newv[r]                     # the new version, then publish
+        yield
+        m.head[r] = (ts, ts, 0)
+        yield
+    out.append(((ts,), reads))
+
+
+def run_mv_schedule(make_txn, scenario, initial, seed):
+    m = MVMem(initial)
+    outs = [[] for _ in scenario]
+    gens = [make_txn(m, ops, outs[i]) for i, ops in enumerate(scenario)]
+    live = list(range(len(gens)))
+    rng = random.Random(seed)
+    while live:
+        i = rng.choice(live)
+        try:
+            next(gens[i])
+        except StopIteration:
+            live.remove(i)
+    committed = [(o[0][0], o[0][1], scenario[i]) for i, o in enumerate(outs) if o]
+    final = [m.versions[r][m.head[r][0]] for r in range(len(initial))]
+    return committed, final
+
+
+def _mv_violations(make_txn, scenario, n):
+    initial = [100, 200, 300]
+    bad = commits = 0
+    for seed in range(n):
+        committed, final = run_mv_schedule(make_txn, scenario, initial, seed)
+        commits += len(committed)
+        if not serial_replay_ok(committed, initial, final):
+            bad += 1
+    return bad, commits
+
+
+@pytest.mark.parametrize("name", sorted(SCENARIOS))
+def test_mvto_design_is_serializable(name):
+    bad, commits = _mv_violations(mvto_txn, SCENARIOS[name], 4000)
+    assert bad == 0
+    assert commits > 0
+
+
+def test_mvto_old_readers_do_not_abort_on_newer_versions():
+    """The point of the versions: a reader older than the head commits where
+    single-version TO aborts it."""
+    sc = SCENARIOS["read-then-overwrite"]
+    mv = _mv_violations(mvto_txn, sc, 3000)[1]
+    to = _count_violations(MODELS["to"], sc, 3000)[1]
+    assert mv > to
+
+
+@pytest.mark.parametrize("variant", [dict(raise_rts=False), dict(check_rts=False)])
+def test_mvto_without_the_read_timestamp_is_not_serializable(variant):
+    """Negative controls: a read that does not raise the head's rts, or a
+    writer that ignores it, lets a writer older than a reader slip under it."""
+    make = lambda m, ops, out: mvto_txn(m, ops, out, **variant)
+    bad = sum(_mv_violations(make, SCENARIOS[n], 4000)[0] for n in SCENARIOS)
+    assert bad > 0
