@@ -278,6 +278,16 @@ uint64_t gcc_table_bytes(const gcc_db *db, uint32_t table_id);
 gcc_status gcc_load_table(gcc_db *db, uint32_t table_id, const void *src,
                           uint64_t nbytes, int src_on_device);
 
+/* Fill key-value table 0 on the device with seeded initial values and reset
+ * the concurrency-control words, as gcc_load_table does (synchronous).  Slot
+ * (key, field) takes output number key * n_fields + field + 1 of splitmix64
+ * seeded with `seed` (the YCSB-shaped table of Sec. IV-A, generated where it
+ * lives instead of copied in); a 16-byte slot holds that output in bytes 0-7,
+ * the low 16 bits of the same output number under the seed splitmix64(seed, 2)
+ * in bytes 8-9, and zeros in bytes 10-15.  Errors: GCC_ERR_INVALID (NULL db,
+ * an order-entry database, table_id != 0), GCC_ERR_CUDA. */
+gcc_status gcc_init_table_seeded(gcc_db *db, uint32_t table_id, uint64_t seed);
+
 /* Copy table table_id out (synchronous; waits for prior work on the stream). */
 gcc_status gcc_db_read_table(gcc_db *db, uint32_t table_id, void *dst,
                              uint64_t nbytes, int dst_on_device);

@@ -539,6 +539,23 @@ gcc_status gcc_load_table(gcc_db* db, uint32_t id, const void* src, uint64_t nby
     return GCC_OK;
 }
 
+gcc_status gcc_init_table_seeded(gcc_db* db, uint32_t id, uint64_t seed) {
+    if (!db) return fail(GCC_ERR_INVALID, "null database");
+    if (db->d.schema != GCC_SCHEMA_KV)
+        return fail(GCC_ERR_INVALID,
+                    "seeded initialisation is for key-value tables (order-entry tables load "
+                    "with gcc_load_table)");
+    if (id != 0) return fail(GCC_ERR_INVALID, "no table %u", id);
+    GCC_CK(cudaSetDevice(db->d.device));
+    GCC_CK(cudaDeviceSynchronize());
+    GCC_CK(gcc::launch_seeded_init(db->table, db->d.n_records, db->d.n_fields, db->d.field_bytes,
+                                   seed, db->sm_count, 0));
+    GCC_CK(cudaMemset(db->meta, 0, db->n_meta * 16));
+    db->meta_state = META_ZERO;
+    GCC_CK(cudaDeviceSynchronize());
+    return GCC_OK;
+}
+
 gcc_status gcc_db_read_table(gcc_db* db, uint32_t id, void* dst, uint64_t nbytes,
                              int dst_on_device) {
     if (!db || !dst) return fail(GCC_ERR_INVALID, "null argument");

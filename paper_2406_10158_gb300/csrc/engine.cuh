@@ -348,5 +348,9 @@ cudaError_t det_fold_kv(const ExecArgs& a, uint32_t field_bytes, SortScratch& s,
 cudaError_t densify_commit_order(const ExecArgs& a, SortScratch& s, cudaStream_t st);
 // TicToc: dense ranks in (timestamp, sequence number) order.
 cudaError_t densify_tictoc(const ExecArgs& a, SortScratch& s, cudaStream_t st);
+// Seeded initial values of a key-value table, written on the device.
+cudaError_t launch_seeded_init(uint8_t* table, uint64_t n_records, uint32_t n_fields,
+                               uint32_t field_bytes, uint64_t seed, int sm_count,
+                               cudaStream_t st);
 
 }  // namespace gcc

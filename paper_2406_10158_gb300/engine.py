@@ -159,6 +159,7 @@ SIGNATURES = {
     "gcc_table_bytes": (ctypes.c_uint64, [P, ctypes.c_uint32]),
     "gcc_load_table": (ctypes.c_int, [P, ctypes.c_uint32, P, ctypes.c_uint64, ctypes.c_int]),
     "gcc_db_read_table": (ctypes.c_int, [P, ctypes.c_uint32, P, ctypes.c_uint64, ctypes.c_int]),
+    "gcc_init_table_seeded": (ctypes.c_int, [P, ctypes.c_uint32, ctypes.c_uint64]),
     "gcc_default_params": (ctypes.c_int, [ctypes.POINTER(ExecParams)]),
     "gcc_txn_batch_submit": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_uint32, P, P,
                                             ctypes.c_uint64, ctypes.c_int,
@@ -265,6 +266,10 @@ def gcc_db_destroy(db: int):
 
 def gcc_load_table(db: int, table_id: int, src_ptr: int, nbytes: int, on_device: bool):
     _check(load().gcc_load_table(db, table_id, src_ptr, nbytes, int(on_device)))
+
+
+def gcc_init_table_seeded(db: int, table_id: int, seed: int):
+    _check(load().gcc_init_table_seeded(db, table_id, seed & ((1 << 64) - 1)))
 
 
 def gcc_db_read_table(db: int, table_id: int, dst_ptr: int, nbytes: int, on_device: bool):
@@ -430,6 +435,10 @@ class Database:
     # key-value helpers -----------------------------------------------------
     def load_kv(self, table: np.ndarray):
         self.load_table(0, table)
+
+    def init_seeded(self, seed: int):
+        """Fill the key-value table on the device (see workload.kv_table_seeded)."""
+        gcc_init_table_seeded(self.handle, 0, seed)
 
     def read_kv(self) -> np.ndarray:
         d = self.desc

@@ -208,6 +208,18 @@ def kv_table_splitmix(seed: int, nrec: int, nfields: int) -> np.ndarray:
     return out
 
 
+def kv_table_seeded(seed: int, nrec: int, nfields: int, field_bytes: int = 8) -> np.ndarray:
+    """The table gcc_init_table_seeded writes on the device: 8-byte slots as
+    kv_table_splitmix; 16-byte slots (uint64[nfields, nrec, 2]) hold that value
+    in bytes 0-7 and the low 16 bits of the same output number under the seed
+    splitmix64(seed, 2) in bytes 8-9."""
+    lo = kv_table_splitmix(seed, nrec, nfields)
+    if field_bytes == 8:
+        return lo
+    hi = kv_table_splitmix(int(splitmix64_at(seed, 2)), nrec, nfields) & np.uint64(0xFFFF)
+    return np.stack([lo, hi], axis=-1)
+
+
 def kv_table_bytes(seed: int, nrec: int, nfields: int, payload_bytes: int = 10) -> np.ndarray:
     """uint64[nfields, nrec, 2]: 16-byte slots whose first ``payload_bytes``
     bytes are uniform random and whose remaining bytes are zero."""

@@ -85,6 +85,7 @@ def test_null_handles(lib):
     buf = ctypes.create_string_buffer(16)
     expect(lib, lib.gcc_load_table(None, 0, buf, 16, 0), INVALID, ["null"])
     expect(lib, lib.gcc_db_read_table(None, 0, buf, 16, 0), INVALID, ["null"])
+    expect(lib, lib.gcc_init_table_seeded(None, 0, 1), INVALID, ["null"])
     expect(lib, lib.gcc_execute(None, 0, None, 0, None, None, 0, None, None, None, None),
            INVALID, ["null database"])
     expect(lib, lib.gcc_last_stats(None, None), INVALID, ["null"])

@@ -166,6 +166,24 @@ def test_edge_cases(eng, scheme):
             db.submit("det" if scheme.startswith("det") else scheme, big)
 
 
+@pytest.mark.parametrize("field_bytes", [8, 16])
+def test_seeded_init_on_the_device(eng, field_bytes):
+    """gcc_init_table_seeded writes the generator's table bit for bit and
+    resets the control words: a batch afterwards replays from that table."""
+    nrec, nfields = 3001, 3                         # slots not a multiple of the block
+    table = wl.kv_table_seeded(0x5EED0009, nrec, nfields, field_bytes)
+    with eng.Database("kv", n_records=nrec, n_fields=nfields, field_bytes=field_bytes,
+                      max_batch_txns=2048) as db:
+        db.init_seeded(0x5EED0009)
+        assert np.array_equal(db.read_kv(), table)
+        batch = wl.kv_batch(12, nrec=nrec, nfields=nfields, n_txns=2048, theta=0.8,
+                            field_bytes=field_bytes)
+        res, reads, stats = go(eng, db, "occ", batch)
+        check(table, db.read_kv(), batch, res, reads, "occ", stats)
+        db.init_seeded(0x5EED0009)                    # again, after the batch
+        assert np.array_equal(db.read_kv(), table)
+
+
 def test_outstanding_batch_limit(eng):
     """Up to GCC_MAX_OUTSTANDING_BATCHES (256) submitted batches may be pending
     on one database; one more is refused with GCC_ERR_CAPACITY until a batch
