@@ -190,6 +190,25 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def host_info() -> dict:
+    """The host the CPU baseline ran on: its core count and CPU model."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            fields = {}
+            for line in f:
+                k, _, v = line.partition(":")
+                fields.setdefault(k.strip(), v.strip())
+        model = fields.get("model name")
+        if not model and "CPU part" in fields:   # Arm: implementer and part numbers
+            model = f"implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "machine": platform.machine(),
+            "cpu": model or platform.processor() or "unknown"}
+
+
 def time_oracle(table, batch, seconds: float, max_txns=None):
     """Single-threaded serial execution (the CPU oracle) of a prefix of the
     batch, repeated until about ``seconds`` have passed; returns txn/s."""
@@ -240,7 +259,8 @@ def run_reference(args, rank, world):
             "config": workload,
             "cpu_baseline": {"value": value, "unit": "txn/s", "cores": 1, "kind": "oracle",
                              "sample": f"first {sample} of {batch.n_txns} txns per step, "
-                                       "serial in transaction-id order"},
+                                       "serial in transaction-id order",
+                             "host": host_info()},
             "e2e": {"value": value, "unit": "txn/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -408,7 +428,8 @@ def run_ours(args, rank, world, dist):
         v, info = time_oracle(table, batch, args.cpu_seconds, max_txns=1 << 18)
         cpu = {"value": v, "unit": "txn/s", "cores": 1, "kind": "oracle",
                "sample": f"first {info['txns']} txns of the batch, serial in id order, "
-                         f"{info['repeats']} repeats, {info['seconds']} s"}
+                         f"{info['repeats']} repeats, {info['seconds']} s",
+               "host": host_info()}
     out = {"metric": METRIC, "value": value, "unit": "txn/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",

@@ -55,3 +55,10 @@ def test_captured_traffic_only_for_the_captured_workload():
         assert k == key
     assert bench.CAPTURED_TRAFFIC.get(("occ", 1 << 24, 1 << 20, 0.6, 0.5, 0, 0)) is None
     assert bench.CAPTURED_TRAFFIC.get(("2pl", 1 << 24, 1 << 20, 0.8, 0.5, 0, 0)) is None
+
+
+def test_host_info_names_cores_and_model():
+    h = bench.host_info()
+    assert h["nproc"] == os.cpu_count() and h["nproc"] >= 1
+    assert isinstance(h["cpu"], str) and h["cpu"]
+    assert h["machine"]
