@@ -137,6 +137,44 @@ def algorithmic_bytes(batch) -> dict:
     return {"bytes": total, "reads": n_r, "writes": n_w, "per_txn": total / max(1, batch.n_txns)}
 
 
+# Useful bytes of one order-entry op by kind (8-byte descriptor, 16-byte value
+# out; control word read + revalidated, or locked + unlocked, 8 + 8; the int64
+# columns the procedure reads and writes; 16-byte operand where it has one).
+OE_OP_BYTES = {
+    "w_read": 8 + 16 + 16 + 8,                        # w_tax
+    "d_neworder": 8 + 16 + 16 + 8 + 8 + 8,            # d_next_o_id r/w, d_tax
+    "c_read": 8 + 16 + 16 + 8 + 8,                    # c_discount, c_balance
+    "i_read": 8 + 16 + 8,                             # i_price, no control word
+    "s_neworder": 8 + 16 + 16 + 16 + 4 * 16,          # s_quantity, s_order_cnt, s_ytd,
+                                                      # s_remote_cnt read and written
+    "w_pay": 8 + 16 + 16 + 16 + 16,                   # w_ytd r/w
+    "d_pay": 8 + 16 + 16 + 16 + 16,                   # d_ytd r/w
+    "c_pay": 8 + 16 + 16 + 16 + 3 * 16,               # c_balance, c_payment_cnt,
+}                                                     # c_ytd_payment read and written
+OE_ORDER_INSERT = 4 * 8                               # o_c_id, o_ol_cnt, o_all_local, no_flag
+OE_LINE_INSERT = 4 * 8                                # ol_i_id, ol_supply_w_id, ol_quantity,
+                                                      # ol_amount
+
+
+def oe_algorithmic_bytes(batch) -> dict:
+    """Useful bytes of an order-entry batch: per transaction its 8-byte
+    descriptor and 16-byte result, per op OE_OP_BYTES of its kind, and the
+    rows a NewOrder inserts (its order and new-order row, and one row per
+    line)."""
+    from paper_2406_10158_gb300 import workload as wl
+    kinds = {wl.OE_W_READ: "w_read", wl.OE_D_NEWORDER: "d_neworder", wl.OE_C_READ: "c_read",
+             wl.OE_I_READ: "i_read", wl.OE_S_NEWORDER: "s_neworder", wl.OE_W_PAY: "w_pay",
+             wl.OE_D_PAY: "d_pay", wl.OE_C_PAY: "c_pay"}
+    count = np.bincount(batch.ops["kind"].astype(np.int64), minlength=32)
+    total = batch.n_txns * (8 + 16)
+    for k, name in kinds.items():
+        total += int(count[k]) * OE_OP_BYTES[name]
+    total += int(count[wl.OE_D_NEWORDER]) * OE_ORDER_INSERT + int(count[wl.OE_S_NEWORDER]) * OE_LINE_INSERT
+    return {"bytes": total, "new_orders": int(count[wl.OE_D_NEWORDER]),
+            "payments": int(count[wl.OE_W_PAY]), "lines": int(count[wl.OE_S_NEWORDER]),
+            "per_txn": total / max(1, batch.n_txns)}
+
+
 def hot_record_counts(batch) -> dict:
     """Accesses and writes of the most accessed / most written record."""
     from paper_2406_10158_gb300 import workload as wl

@@ -62,3 +62,16 @@ def test_host_info_names_cores_and_model():
     assert h["nproc"] == os.cpu_count() and h["nproc"] >= 1
     assert isinstance(h["cpu"], str) and h["cpu"]
     assert h["machine"]
+
+
+def test_order_entry_bytes_by_procedure():
+    """A NewOrder of L lines moves 224 + 184 L useful bytes, a Payment 272:
+    per transaction 24, then its ops and inserts (the byte table's sums)."""
+    _, oe, _ = wl.order_entry(seed=3, W=2, n_txns=400)
+    got = bench.oe_algorithmic_bytes(oe)
+    is_no = oe.txns["type"] == wl.TXN_NEW_ORDER
+    lines = (oe.txns["n_ops"][is_no].astype(np.int64) - 3) // 2
+    want = int((224 + 184 * lines).sum()) + 272 * int((~is_no).sum())
+    assert got["bytes"] == want
+    assert got["new_orders"] == int(is_no.sum()) and got["lines"] == int(lines.sum())
+    assert 900 < got["per_txn"] < 1400            # about 1.2 KB at 50/50 and 10 lines
