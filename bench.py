@@ -693,6 +693,7 @@ def run_sweep(args, rank, world):
                 rs = torch.empty(batch.n_txns * 16, dtype=torch.uint8, device=dev)
                 rd = torch.empty(batch.n_ops * 16, dtype=torch.uint8, device=dev)
                 torch.cuda.synchronize(dev)
+                useful = algorithmic_bytes(batch)["bytes"]
                 reps = 1 if theta >= 0.99 else 3
                 for scheme in SCHEMES:
                     for _ in range(1 + reps):
@@ -703,6 +704,7 @@ def run_sweep(args, rank, world):
                     kv_rows.append({"theta": theta, "read_ratio": rr, "scheme": scheme,
                                     "committed_txn_per_s": st["committed"] / ms * 1e3,
                                     "abort_rate": st["abort_rate"], "ms_per_batch": ms,
+                                    "algorithmic_gbs": useful / ms / 1e6,
                                     "all_committed": st["committed"] == batch.n_txns})
                 db.close()
         for W in (1, 8, 64):
@@ -712,6 +714,7 @@ def run_sweep(args, rank, world):
             tx, op, od = up(batch.txns), up(batch.ops), up(batch.operands)
             rs = torch.empty(batch.n_txns * 16, dtype=torch.uint8, device=dev)
             rd = torch.empty(batch.n_ops * 16, dtype=torch.uint8, device=dev)
+            useful = oe_algorithmic_bytes(batch)["bytes"]
             for scheme in SCHEMES:
                 for _ in range(2):                 # a warm-up batch, then the timed one
                     db.load_oe(db0)               # fresh order slots for the inserts
@@ -723,6 +726,7 @@ def run_sweep(args, rank, world):
                 oe_rows.append({"W": W, "scheme": scheme,
                                 "committed_txn_per_s": st["committed"] / ms * 1e3,
                                 "abort_rate": st["abort_rate"], "ms_per_batch": ms,
+                                "algorithmic_gbs": useful / ms / 1e6,
                                 "all_committed": st["committed"] == batch.n_txns})
             db.close()
     head = next(r for r in kv_rows if r["theta"] == 0.8 and r["read_ratio"] == 0.5
