@@ -258,3 +258,20 @@ def oe_replay_check(init_db: dict, gpu_db: dict, W: int, order_cap: int, batch,
     bad_cols = {c: n for c, n in bad_cols.items() if n}
     return {"ok": bad_reads == 0 and not bad_cols, "n_committed": int(order.size),
             "n_read_mismatch": bad_reads, "bad_columns": bad_cols}
+
+
+def customer_by_last_name(c_last, c_first, name: int) -> int:
+    """The customer a payment by last name selects in one district, given the
+    district's last-name ids and first-name keys: among the customers named
+    ``name``, ordered by first name and then by customer index, the one at
+    position ceil(n/2) (1-based) -- the middle one, the lower of the two
+    middles for an even n.  Returns its index in the district, or -1 when
+    nobody has the name.  (The by-name variant of the order-entry payment;
+    its selection rule is this library's reading, the paper's Sec. IV-A
+    naming only the transaction.)"""
+    named = [c for c in range(len(c_last)) if int(c_last[c]) == name]
+    if not named:
+        return -1
+    named.sort(key=lambda c: (int(c_first[c]), c))
+    return named[(len(named) + 1) // 2 - 1]
+

@@ -368,6 +368,27 @@ def nurand(rng: np.random.Generator, A: int, x: int, y: int, C: int, size) -> np
     return ((a | b) + C) % (y - x + 1) + x
 
 
+OE_LAST_NAMES = 1000
+
+
+def oe_customer_names(seed: int, W: int) -> dict:
+    """Name keys of every customer, rows as the c_ columns: ``c_last`` a
+    last-name id in [0, 1000) -- the first 1,000 customers of each district
+    take ids 0..999 in order, the rest NURand(255, 0, 999), so that every name
+    exists in every district and a few are common -- and ``c_first`` a
+    uniform 32-bit first-name key.  (Names are ids: the engine keeps no
+    strings.)"""
+    rng = np.random.Generator(np.random.PCG64(derive_seed(seed, 22)))
+    n_d = W * OE_DISTRICTS
+    c_run = int(rng.integers(0, 256))
+    last = np.empty((n_d, OE_CUSTOMERS), dtype=np.int64)
+    last[:, :OE_LAST_NAMES] = np.arange(OE_LAST_NAMES)
+    last[:, OE_LAST_NAMES:] = nurand(rng, 255, 0, OE_LAST_NAMES - 1, c_run,
+                                     (n_d, OE_CUSTOMERS - OE_LAST_NAMES))
+    first = rng.integers(0, 1 << 32, size=n_d * OE_CUSTOMERS, dtype=np.int64)
+    return {"c_last": last.ravel(), "c_first": first}
+
+
 def oe_initial_db(seed: int, W: int, order_cap: int) -> dict:
     """The initial order-entry database as a dict of int64 columns.
 

@@ -411,3 +411,59 @@ def test_mutants_are_caught(name, tmp_path):
         except (AssertionError, oracle.OracleError):
             failed.append(pin.__name__)
     assert failed, f"mutant {name} passed every pin"
+
+
+# ---------------------------------------------------------------------------
+# payment by last name: the selection rule (a reading; the kernel is not built)
+# ---------------------------------------------------------------------------
+def _last_name_golden():
+    with open(os.path.join(GOLDEN, "oe_last_name.json")) as f:
+        g = json.load(f)
+    return g["c_last"], g["c_first"], {int(k): v for k, v in g["expected"].items()}
+
+
+def test_customer_by_last_name_golden():
+    last, first, expected = _last_name_golden()
+    for name, want in expected.items():
+        assert oracle.customer_by_last_name(last, first, name) == want, name
+
+
+def test_customer_by_last_name_golden_rejects_plausible_mistakes():
+    """Each plausible misreading of the rule disagrees with the hand-worked
+    fixture somewhere: the upper middle, ties by descending index, no
+    first-name order at all, and counting from zero."""
+    last, first, expected = _last_name_golden()
+
+    def pick(order, position):
+        def f(name):
+            named = [c for c in range(len(last)) if last[c] == name]
+            if not named:
+                return -1
+            return order(named)[position(len(named))]
+        return f
+
+    by_first = lambda named: sorted(named, key=lambda c: (first[c], c))
+    variants = {
+        "upper middle": pick(by_first, lambda n: n // 2),
+        "ties by descending index": pick(lambda named: sorted(named, key=lambda c: (first[c], -c)),
+                                         lambda n: (n + 1) // 2 - 1),
+        "index order": pick(sorted, lambda n: (n + 1) // 2 - 1),
+        "zero-based ceil": pick(by_first, lambda n: min((n + 1) // 2, n - 1)),
+    }
+    for label, f in variants.items():
+        assert any(f(name) != want for name, want in expected.items()), label
+
+
+def test_customer_by_last_name_on_generated_districts():
+    names = wl.oe_customer_names(5, 1)
+    last = names["c_last"].reshape(wl.OE_DISTRICTS, wl.OE_CUSTOMERS)
+    first = names["c_first"].reshape(wl.OE_DISTRICTS, wl.OE_CUSTOMERS)
+    rng = np.random.default_rng(0)
+    for d in range(2):
+        for name in rng.integers(0, wl.OE_LAST_NAMES, size=20):
+            c = oracle.customer_by_last_name(last[d], first[d], int(name))
+            named = np.nonzero(last[d] == name)[0]
+            assert c in named                                  # every name exists
+            key = lambda i: (int(first[d][i]), int(i))
+            before = sum(key(i) < key(c) for i in named)
+            assert before == (named.size + 1) // 2 - 1

@@ -94,3 +94,14 @@ def test_poisson_arrivals_have_the_offered_rate():
     # exponential gaps: mean 1/rate, coefficient of variation 1
     assert abs(gaps.mean() / (1e9 / rate) - 1.0) < 0.01
     assert abs(gaps.std() / gaps.mean() - 1.0) < 0.02
+
+
+def test_customer_names():
+    names = wl.oe_customer_names(3, 2)
+    last = names["c_last"].reshape(2 * wl.OE_DISTRICTS, wl.OE_CUSTOMERS)
+    assert names["c_first"].shape == last.ravel().shape
+    assert (last[:, :wl.OE_LAST_NAMES] == np.arange(wl.OE_LAST_NAMES)).all()
+    assert last.min() >= 0 and last.max() < wl.OE_LAST_NAMES
+    # NURand skews the remaining 2,000 per district towards a few names
+    counts = np.bincount(last[:, wl.OE_LAST_NAMES:].ravel(), minlength=wl.OE_LAST_NAMES)
+    assert counts.max() > 4 * counts.mean()
