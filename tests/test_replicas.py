@@ -55,3 +55,38 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     assert bench.main(["--impl", "reference"]) is None
     assert capsys.readouterr().out == ""
+
+
+@pytest.mark.parametrize("form", ["served", "sweep"])
+def test_one_gpu_forms_run_on_rank_zero_only(monkeypatch, capsys, form):
+    """The served form and the sweep are single-GPU measurements: under
+    torchrun the other ranks return at once, and no process group is made."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import torch.distributed as dist
+    calls = []
+    monkeypatch.setattr(bench, "run_served", lambda *a: calls.append("served") or None)
+    monkeypatch.setattr(bench, "run_sweep", lambda *a: calls.append("sweep") or None)
+    monkeypatch.setattr(dist, "init_process_group",
+                        lambda *a, **k: pytest.fail("no process group for a one-GPU form"))
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    assert bench.main(["--form", form]) is None
+    assert calls == [] and capsys.readouterr().out == ""
+    monkeypatch.setenv("RANK", "0")
+    bench.main(["--form", form])
+    assert calls == [form]
+
+
+def test_batched_form_gets_the_process_group(monkeypatch):
+    """The batched form runs on every rank and receives the process group for
+    its barriers and totals."""
+    sys.path.insert(0, ROOT)
+    import bench
+    seen = []
+    monkeypatch.setattr(bench, "run_batched", lambda args, rank, world, dist: seen.append(
+        (rank, world, dist)) or None)
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setenv("RANK", "0")
+    bench.main(["--form", "batched"])
+    assert seen == [(0, 1, None)]
