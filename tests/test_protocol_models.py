@@ -16,6 +16,7 @@ checking wts again after the value, and TicToc reading (wts, value, rts)
 without re-checking wts.
 """
 import random
+import sys
 
 import pytest
 
@@ -673,3 +674,191 @@ def test_occ_early_hot_locks_commit_more_on_the_hot_record():
         early = _count_violations(make, SCENARIOS[name], 3000)[1]
         plain = _count_violations(MODELS["occ"], SCENARIOS[name], 3000)[1]
         assert early > plain, name
+
+
+# ---------------------------------------------------------------------------
+# The same multi-version TO at the level of the planned device structures.
+# Control words are per record (conflicts at record granularity), values per
+# (record, field) slot.  A record's 16-byte head word is (wts, rts, pending
+# writer, chain), timestamps batch-relative.  Committed writes append
+# immutable entries (wts, field, value, next) to a batch-wide version store
+# (an atomic counter hands out indices), and chain is the newest entry's
+# index + 1 (0: none, the table slot is the record's only version).
+#
+# A read of field f at ts:
+#   - if the head is older than ts, it raises rts by a CAS;
+#   - it then takes the newest entry older than ts that wrote f, walking the
+#     chain from the head, or else the table slot, which nothing writes
+#     during the batch.
+#
+# At the batch's end a flatten pass writes each slot's newest entry into the
+# table and zeroes the heads.
+# ---------------------------------------------------------------------------
+class DevMV:
+    def __init__(self, table):                          # table[record][field]
+        self.table = [list(r) for r in table]
+        self.head = [(0, 0, 0, 0)] * len(table)         # (wts, rts, pend, chain)
+        self.store = []                                 # (wts, field, value, next)
+        self.clock = 0
+
+
+def _dev_value(m, r, f, chain, ts):
+    e = chain
+    while e:
+        wts, field, value, nxt = m.store[e - 1]
+        if wts < ts and field == f:
+            return value
+        e = nxt
+    return m.table[r][f]
+
+
+def dev_mvto_txn(m, ops, out):
+    """ops: (record, field, delta or None)."""
+    m.clock += 1
+    ts = m.clock
+    yield
+    reads, pending = {}, {}
+    fail = False
+    for (r, f, d) in ops:
+        for _ in range(3):
+            h = m.head[r]                               # one 16-byte load
+            w, rt, pend, chain = h
+            yield
+            if d is None:
+                if pend and pend < ts:
+                    fail = True
+                    break
+                if w < ts:
+                    if m.head[r] != h:                  # CAS raising rts
+                        yield
+                        continue
+                    m.head[r] = (w, max(rt, ts), pend, chain)
+                    yield
+                reads[(r, f)] = _dev_value(m, r, f, chain, ts)
+                yield
+                break
+            if pend or w >= ts or rt > ts:
+                fail = True
+                break
+            if m.head[r] != h:                          # CAS installing the pending writer
+                yield
+                continue
+            m.head[r] = (w, rt, ts, chain)
+            old = _dev_value(m, r, f, chain, ts)
+            yield
+            reads[(r, f)] = old
+            pending[r] = (f, old + d)
+            break
+        else:
+            fail = True
+        if fail:
+            break
+    if fail:
+        for r in pending:                               # withdraw by CAS loop
+            w, rt, _, chain = m.head[r]
+            m.head[r] = (w, rt, 0, chain)
+            yield
+        return
+    for r, (f, v) in pending.items():
+        m.store.append(None)                            # index from the counter
+        idx = len(m.store)
+        yield
+        m.store[idx - 1] = (ts, f, v, m.head[r][3])     # the entry, then publish
+        yield
+        m.head[r] = (ts, ts, 0, idx)                    # CAS loop: only rts can move
+        yield
+    out.append(((ts,), reads))
+
+
+def dev_flatten(m):
+    for r, (_, _, _, chain) in enumerate(m.head):
+        seen = set()
+        e = chain
+        while e:
+            wts, f, v, nxt = m.store[e - 1]
+            if f not in seen:
+                m.table[r][f] = v
+                seen.add(f)
+            e = nxt
+        m.head[r] = (0, 0, 0, 0)
+    m.store.clear()
+
+
+DEV_SCENARIOS = {
+    "fields of one record": [[(0, 0, None), (1, 1, 5)], [(0, 1, 3)], [(0, 0, 2), (1, 0, None)]],
+    "write skew": [[(0, 0, None), (1, 0, 4)], [(1, 0, None), (0, 0, 6)]],
+    "hot record": [[(0, 0, 1)], [(0, 1, 2)], [(0, 0, None), (1, 1, 7)], [(0, 0, 3), (1, 1, None)]],
+    "old reader behind other fields": [[(0, 0, 1)], [(0, 1, 2)], [(0, 0, None)], [(0, 0, 3)],
+                                       [(0, 1, 4)], [(0, 1, None)]],
+}
+
+
+def _dev_replay(committed, initial, final):
+    val = [list(r) for r in initial]
+    for _, reads, ops in sorted(committed, key=lambda c: c[0]):
+        for (r, f, d) in ops:
+            if val[r][f] != reads[(r, f)]:
+                return False
+            if d is not None:
+                val[r][f] += d
+    return val == final
+
+
+def _dev_runs(scenario, n, flatten=None):
+    """(violations, commits) over n seeded interleavings, flattened at the end."""
+    initial = [[100, 200], [300, 400]]
+    bad = commits = 0
+    for seed in range(n):
+        m = DevMV(initial)
+        outs = [[] for _ in scenario]
+        gens = [dev_mvto_txn(m, ops, outs[i]) for i, ops in enumerate(scenario)]
+        live = list(range(len(gens)))
+        rng = random.Random(seed)
+        while live:
+            i = rng.choice(live)
+            try:
+                next(gens[i])
+            except StopIteration:
+                live.remove(i)
+        (flatten or dev_flatten)(m)
+        assert m.head == [(0, 0, 0, 0)] * len(initial) and not m.store
+        committed = [(o[0][0], o[0][1], scenario[i]) for i, o in enumerate(outs) if o]
+        commits += len(committed)
+        bad += not _dev_replay(committed, initial, m.table)
+    return bad, commits
+
+
+@pytest.mark.parametrize("name", sorted(DEV_SCENARIOS))
+def test_device_mvto_layout_is_serializable(name):
+    bad, commits = _dev_runs(DEV_SCENARIOS[name], 3000)
+    assert bad == 0
+    assert commits > 0
+
+
+def test_device_mvto_flatten_must_take_the_newest_entry(monkeypatch):
+    """Negative control: a flatten that lets the oldest entry of a slot win."""
+    def oldest_wins(m):
+        for r, (_, _, _, chain) in enumerate(m.head):
+            e = chain
+            while e:
+                _, f, v, nxt = m.store[e - 1]
+                m.table[r][f] = v
+                e = nxt
+            m.head[r] = (0, 0, 0, 0)
+        m.store.clear()
+    assert _dev_runs(DEV_SCENARIOS["old reader behind other fields"], 3000, oldest_wins)[0] > 0
+
+
+def test_device_mvto_walk_must_match_the_field(monkeypatch):
+    """Negative control: a walk that stops at the first entry older than the
+    reader whatever field it wrote."""
+    def first_older(m, r, f, chain, ts):
+        e = chain
+        while e:
+            wts, field, value, nxt = m.store[e - 1]
+            if wts < ts:
+                return value if field == f else m.table[r][f]
+            e = nxt
+        return m.table[r][f]
+    monkeypatch.setattr(sys.modules[__name__], "_dev_value", first_older)
+    assert _dev_runs(DEV_SCENARIOS["old reader behind other fields"], 3000)[0] > 0
