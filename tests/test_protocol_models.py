@@ -862,3 +862,155 @@ def test_device_mvto_walk_must_match_the_field(monkeypatch):
         return m.table[r][f]
     monkeypatch.setattr(sys.modules[__name__], "_dev_value", first_older)
     assert _dev_runs(DEV_SCENARIOS["old reader behind other fields"], 3000)[0] > 0
+
+
+# ---------------------------------------------------------------------------
+# Whole batches with retries, in parallel rounds: every live transaction
+# takes one memory step per round (the GPU runs them side by side); an
+# aborted one restarts after a randomized backoff (rounds, doubling with its
+# aborts).  With early locks, a transaction that aborted on a record it
+# writes locks that record in its next attempts (occ_retry_txn below mirrors
+# the early-lock kernel: the record is locked after the read phase, with a
+# bounded wait).  The histories must replay, and the round count compares
+# the two policies on a batch with one hot record.
+# ---------------------------------------------------------------------------
+def occ_retry_txn(m, ops, out, info, early=None, wait_steps=64):
+    obs, reads, newv, held = {}, {}, {}, []
+
+    def release():
+        for h in held:
+            m.word[h] = obs[h]
+
+    for (r, d) in ops:
+        if r == early and d is not None:
+            continue                                    # read under its lock below
+        v1 = m.word[r]
+        yield
+        if v1 & LOCK:
+            info["crec"] = r
+            return
+        x = m.val[r]
+        yield
+        obs[r], reads[r] = v1, x
+        if d is not None:
+            newv[r] = x + d
+    de = next((d for r, d in ops if r == early and d is not None), None)
+    if de is not None:
+        for _ in range(wait_steps + 1):
+            v = m.word[early]
+            if not (v & LOCK):
+                m.word[early] = v | LOCK                # the CAS
+                obs[early] = v
+                held.append(early)
+                yield
+                break
+            yield
+        else:
+            info["crec"] = early
+            return
+        x = m.val[early]
+        yield
+        reads[early], newv[early] = x, x + de
+    for (r, d) in ops:
+        if d is None or r in held:
+            continue
+        if m.word[r] != obs[r]:
+            info["crec"] = r
+            release()
+            return
+        m.word[r] = obs[r] | LOCK
+        held.append(r)
+        yield
+    ts = m.clock
+    m.clock += 1
+    yield
+    for (r, d) in ops:
+        if d is None:
+            ok = m.word[r] == obs[r]
+            yield
+            if not ok:
+                info["crec"] = r
+                release()
+                return
+    for r in held:
+        m.val[r] = newv[r]
+        yield
+    for r in held:
+        m.word[r] = ts + 1
+        yield
+    out.append(((ts,), reads))
+
+
+def run_batch_rounds(txns, nrec, seed, early_after=0, max_rounds=100000):
+    """(rounds to commit everything, aborts, history replays, committed)."""
+    rng = random.Random(seed)
+    initial = [100 + i for i in range(nrec)]
+    m = Mem(initial)
+    n = len(txns)
+    outs = [[] for _ in range(n)]
+    state, info = [None] * n, [dict() for _ in range(n)]
+    aborts, early = [0] * n, [None] * n
+
+    def start(i):
+        info[i] = {}
+        state[i] = occ_retry_txn(m, txns[i], outs[i], info[i], early[i])
+
+    for i in range(n):
+        start(i)
+    done = rounds = 0
+    while done < n and rounds < max_rounds:
+        rounds += 1
+        order = list(range(n))
+        rng.shuffle(order)
+        for i in order:
+            s = state[i]
+            if s is None:
+                continue
+            if isinstance(s, int):                      # backing off until round s
+                if rounds >= s:
+                    start(i)
+                continue
+            try:
+                next(s)
+            except StopIteration:
+                if outs[i]:
+                    state[i] = None
+                    done += 1
+                    continue
+                aborts[i] += 1
+                c = info[i].get("crec")
+                if (early_after and c is not None and aborts[i] >= early_after
+                        and any(r == c and d is not None for r, d in txns[i])):
+                    early[i] = c
+                state[i] = rounds + 1 + rng.randint(0, min(1 << min(aborts[i], 10), 64))
+    committed = [(outs[i][0][0], outs[i][0][1], txns[i]) for i in range(n) if outs[i]]
+    return rounds, sum(aborts), serial_replay_ok(committed, initial, m.val), done
+
+
+def hot_batch(seed, n=96, nrec=64, ops=4, hot_share=0.5, read_ratio=0.5):
+    """Transactions of `ops` distinct records; record 0 is in `hot_share` of them."""
+    rng = random.Random(seed)
+    txns = []
+    for _ in range(n):
+        keys = {0} if rng.random() < hot_share else set()
+        while len(keys) < ops:
+            keys.add(rng.randrange(1, nrec))
+        txns.append([(k, None if rng.random() < read_ratio else rng.randint(1, 9))
+                     for k in sorted(keys)])
+    return txns
+
+
+@pytest.mark.parametrize("early_after", [0, 1, 3])
+def test_batches_with_retries_replay(early_after):
+    for seed in range(6):
+        rounds, aborts, ok, done = run_batch_rounds(hot_batch(seed), 64, seed, early_after)
+        assert ok and done == 96, (seed, rounds, aborts)
+
+
+def test_early_locks_take_fewer_rounds_on_a_hot_batch():
+    """In the round model, early locks shorten the hot record's chain more
+    than they delay its readers (read ratios 0.5 and 0: writers dominate)."""
+    for rr in (0.5, 0.0):
+        plain = sum(run_batch_rounds(hot_batch(s, read_ratio=rr), 64, s, 0)[0] for s in range(6))
+        early = sum(run_batch_rounds(hot_batch(s, read_ratio=rr), 64, s, 1)[0] for s in range(6))
+        assert early < plain, (rr, early, plain)
