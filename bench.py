@@ -33,34 +33,39 @@ SCHEMES = ["occ", "2pl", "2pl_wd", "to", "tictoc", "det"]
 
 def parse_args(argv=None):
     p = argparse.ArgumentParser(description=__doc__)
-    p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
-    p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--scheme", default="occ", choices=SCHEMES)
-    p.add_argument("--theta", type=float, default=0.8)
-    p.add_argument("--read-ratio", type=float, default=0.5)
-    p.add_argument("--records", type=int, default=1 << 24)
-    p.add_argument("--txns", type=int, default=1 << 20)
+    p.add_argument("--gpus", type=int, default=1,
+                   help="GPUs (one replica each; under torchrun, the world size)")
+    p.add_argument("--steps", type=int, default=20, help="timed batches")
+    p.add_argument("--warmup", type=int, default=3, help="untimed batches before them")
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours",
+                   help="ours: the engine; reference: the CPU oracle on the same workload")
+    p.add_argument("--scheme", default="occ", choices=SCHEMES, help="scheme of the headline line")
+    p.add_argument("--theta", type=float, default=0.8, help="Zipf skew of the keys (0: uniform)")
+    p.add_argument("--read-ratio", type=float, default=0.5, help="share of READ ops")
+    p.add_argument("--records", type=int, default=1 << 24, help="key-value records")
+    p.add_argument("--txns", type=int, default=1 << 20, help="transactions per batch")
     p.add_argument("--lanes", type=int, default=0, help="lanes per transaction (0 = default)")
     p.add_argument("--warps", type=int, default=0, help="warps per block (0 = default)")
     p.add_argument("--no-schemes", action="store_true", help="skip the per-scheme lines")
-    p.add_argument("--scheme-steps", type=int, default=3)
+    p.add_argument("--scheme-steps", type=int, default=3, help="timed batches per scheme line")
     p.add_argument("--scheme-deadline-s", type=float, default=20.0,
                    help="kernel deadline for the per-scheme lines")
-    p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=10.0)
-    p.add_argument("--seed", type=int, default=0x5EED0002)
+    p.add_argument("--no-e2e", action="store_true",
+                   help="skip the end-to-end measurement through submit/wait")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--cpu-seconds", type=float, default=10.0,
+                   help="about how long the CPU baseline runs")
+    p.add_argument("--seed", type=int, default=0x5EED0002, help="workload seed")
     p.add_argument("--form", choices=["plain", "batched", "served", "sweep"], default="plain",
                    help="plain: one batch per launch (the default line); batched: 64 "
                         "databases in one persistent launch vs 64 plain launches; served: "
                         "continuous batching of a Poisson trace vs plain per-batch launches; "
                         "sweep: every scheme across the key-value contention levels and the "
                         "order-entry warehouse counts")
-    p.add_argument("--n-db", type=int, default=64)
-    p.add_argument("--rates", default="1e5,1e6,1e7,1e8")
-    p.add_argument("--requests", type=int, default=1 << 18)
+    p.add_argument("--n-db", type=int, default=64, help="batched form: databases")
+    p.add_argument("--rates", default="1e5,1e6,1e7,1e8",
+                   help="served form: offered rates (txn/s), comma-separated")
+    p.add_argument("--requests", type=int, default=1 << 18, help="served form: requests per rate")
     p.add_argument("--kv-scheme", default="det", choices=SCHEMES, help="served form: key-value lane")
     p.add_argument("--oe-scheme", default="det", choices=SCHEMES, help="served form: order-entry lane")
     return p.parse_args(argv)
