@@ -712,8 +712,11 @@ def _dev_value(m, r, f, chain, ts):
     return m.table[r][f]
 
 
-def dev_mvto_txn(m, ops, out):
-    """ops: (record, field, delta or None)."""
+def dev_mvto_txn(m, ops, out, raise_by_max=False):
+    """ops: (record, field, delta or None).  raise_by_max: a reader raises
+    rts by an atomic max on its own 32-bit field (which never fails) and then
+    reads the head again, retrying if wts, the pending mark or the chain moved
+    -- instead of one CAS over the whole head."""
     m.clock += 1
     ts = m.clock
     yield
@@ -728,7 +731,15 @@ def dev_mvto_txn(m, ops, out):
                 if pend and pend < ts:
                     fail = True
                     break
-                if w < ts:
+                if w < ts and raise_by_max:
+                    cw, crt, cp, cc = m.head[r]         # atomic max on the rts field
+                    m.head[r] = (cw, max(crt, ts), cp, cc)
+                    yield
+                    w2, _, p2, c2 = m.head[r]           # the head again
+                    yield
+                    if (w2, p2, c2) != (w, pend, chain):
+                        continue
+                elif w < ts:
                     if m.head[r] != h:                  # CAS raising rts
                         yield
                         continue
@@ -804,14 +815,14 @@ def _dev_replay(committed, initial, final):
     return val == final
 
 
-def _dev_runs(scenario, n, flatten=None):
+def _dev_runs(scenario, n, flatten=None, raise_by_max=False):
     """(violations, commits) over n seeded interleavings, flattened at the end."""
     initial = [[100, 200], [300, 400]]
     bad = commits = 0
     for seed in range(n):
         m = DevMV(initial)
         outs = [[] for _ in scenario]
-        gens = [dev_mvto_txn(m, ops, outs[i]) for i, ops in enumerate(scenario)]
+        gens = [dev_mvto_txn(m, ops, outs[i], raise_by_max) for i, ops in enumerate(scenario)]
         live = list(range(len(gens)))
         rng = random.Random(seed)
         while live:
@@ -828,11 +839,59 @@ def _dev_runs(scenario, n, flatten=None):
     return bad, commits
 
 
+@pytest.mark.parametrize("raise_by_max", [False, True])
 @pytest.mark.parametrize("name", sorted(DEV_SCENARIOS))
-def test_device_mvto_layout_is_serializable(name):
-    bad, commits = _dev_runs(DEV_SCENARIOS[name], 3000)
+def test_device_mvto_layout_is_serializable(name, raise_by_max):
+    bad, commits = _dev_runs(DEV_SCENARIOS[name], 3000, raise_by_max=raise_by_max)
     assert bad == 0
     assert commits > 0
+
+
+def test_device_mvto_max_raise_needs_the_second_look(monkeypatch):
+    """Negative control: raising rts by max without reading the head again
+    lets a writer that installed itself in between slip under the reader."""
+    def blind(m, ops, out):
+        m.clock += 1
+        ts = m.clock
+        yield
+        reads, pending = {}, {}
+        for (r, f, d) in ops:
+            w, rt, pend, chain = m.head[r]
+            yield
+            if d is None:
+                if pend and pend < ts:
+                    break
+                if w < ts:
+                    cw, crt, cp, cc = m.head[r]
+                    m.head[r] = (cw, max(crt, ts), cp, cc)
+                    yield
+                reads[(r, f)] = _dev_value(m, r, f, chain, ts)
+                yield
+                continue
+            if pend or w >= ts or rt > ts or m.head[r] != (w, rt, pend, chain):
+                break
+            m.head[r] = (w, rt, ts, chain)
+            reads[(r, f)] = old = _dev_value(m, r, f, chain, ts)
+            pending[r] = (f, old + d)
+            yield
+        else:
+            for r, (f, v) in pending.items():
+                m.store.append(None)
+                idx = len(m.store)
+                yield
+                m.store[idx - 1] = (ts, f, v, m.head[r][3])
+                yield
+                m.head[r] = (ts, ts, 0, idx)
+                yield
+            out.append(((ts,), reads))
+            return
+        for r in pending:
+            w, rt, _, chain = m.head[r]
+            m.head[r] = (w, rt, 0, chain)
+            yield
+    monkeypatch.setattr(sys.modules[__name__], "dev_mvto_txn", lambda m, o, out, rbm=False: blind(m, o, out))
+    bad = sum(_dev_runs(DEV_SCENARIOS[n], 3000)[0] for n in DEV_SCENARIOS)
+    assert bad > 0
 
 
 def test_device_mvto_flatten_must_take_the_newest_entry(monkeypatch):
