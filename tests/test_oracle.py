@@ -310,6 +310,98 @@ def pin_oe_invariants(lib):
     assert fin["d_next_o_id"].sum() - db["d_next_o_id"].sum() == int(no.sum())
 
 
+def _oe_consistent_db(lib):
+    """A consistent order-entry database: a random mix run serially."""
+    W = 2
+    db, batch, cap = wl.order_entry(seed=99, W=W, n_txns=3000)
+    order = np.random.default_rng(1).permutation(batch.n_txns)
+    fin, _ = oracle.oe_serial(db, W, cap, batch, order=order, lib=lib)
+    return W, cap, db, batch, order, fin
+
+
+def pin_oe_consistency_flags_each_violation(lib):
+    """The consistency check reports each of its three conditions by its own
+    bit and nothing else: a district whose next order id is one past its
+    newest order (bit 1), a warehouse whose year-to-date differs from the sum
+    of its districts' (bit 2), and an order line present beyond its order's
+    line count (bit 4)."""
+    W, cap, _, _, _, fin = _oe_consistent_db(lib)
+    assert oracle.oe_consistency(fin, W, cap, lib=lib) == 0
+
+    bad = {c: a.copy() for c, a in fin.items()}
+    bad["d_next_o_id"][7] += 1
+    assert oracle.oe_consistency(bad, W, cap, lib=lib) == 1
+
+    bad = {c: a.copy() for c, a in fin.items()}
+    bad["d_next_o_id"][3] -= 1
+    assert oracle.oe_consistency(bad, W, cap, lib=lib) == 1
+
+    bad = {c: a.copy() for c, a in fin.items()}
+    bad["w_ytd"][1] += 1
+    assert oracle.oe_consistency(bad, W, cap, lib=lib) == 2
+
+    bad = {c: a.copy() for c, a in fin.items()}
+    bad["d_ytd"][4] -= 5            # district 4 belongs to warehouse 0
+    assert oracle.oe_consistency(bad, W, cap, lib=lib) == 2
+
+    bad = {c: a.copy() for c, a in fin.items()}
+    slot = 12 * cap + 5             # an initial order of district 12
+    cnt = int(bad["o_ol_cnt"][slot])
+    assert 0 < cnt < 15
+    bad["ol_quantity"][slot * 15 + cnt] = 3
+    assert oracle.oe_consistency(bad, W, cap, lib=lib) == 4
+
+    bad = {c: a.copy() for c, a in fin.items()}
+    bad["ol_quantity"][slot * 15] = 0   # a line missing inside the count
+    assert oracle.oe_consistency(bad, W, cap, lib=lib) == 4
+
+    bad = {c: a.copy() for c, a in fin.items()}
+    bad["d_next_o_id"][0] += 1
+    bad["w_ytd"][0] += 1
+    assert oracle.oe_consistency(bad, W, cap, lib=lib) == 3
+
+
+def pin_oe_replay_rejects_wrong_outcomes(lib):
+    """The order-entry replay check accepts the order that produced an
+    outcome and rejects: two payments to one district swapped in the commit
+    order (their year-to-date reads differ), one flipped read value, and one
+    corrupted word of a final column."""
+    W, cap, db, batch, order, fin = _oe_consistent_db(lib)
+    _, reads = oracle.oe_serial(db, W, cap, batch, order=order, lib=lib)
+    res = np.zeros(batch.n_txns, dtype=wl.RESULT_DTYPE)
+    res["status"] = oracle.ST_COMMITTED
+    res["commit_order"][order] = np.arange(batch.n_txns)
+    rep = oracle.oe_replay_check(db, fin, W, cap, batch, res, reads, lib=lib)
+    assert rep["ok"] and rep["n_committed"] == batch.n_txns, rep
+
+    # two payments on the same district, adjacent in the commit order
+    pay = batch.txns["type"] == wl.TXN_PAYMENT
+    dist = batch.ops["key"][batch.txns["first_op"].astype(np.int64) + 1]
+    pos = {}
+    for i, t in enumerate(order):
+        if pay[t]:
+            pos.setdefault(int(dist[t]), []).append(i)
+    pair = next((p[k], p[k + 1]) for p in pos.values() for k in range(len(p) - 1)
+                if p[k + 1] == p[k] + 1)
+    swapped = res.copy()
+    a, b = order[pair[0]], order[pair[1]]
+    swapped["commit_order"][a], swapped["commit_order"][b] = pair[1], pair[0]
+    rep = oracle.oe_replay_check(db, fin, W, cap, batch, swapped, reads, lib=lib)
+    assert not rep["ok"] and rep["n_read_mismatch"] >= 2, rep
+
+    flipped = reads.copy()
+    flipped[17, 0] ^= np.uint64(1)
+    rep = oracle.oe_replay_check(db, fin, W, cap, batch, res, flipped, lib=lib)
+    assert not rep["ok"] and rep["n_read_mismatch"] == 1, rep
+
+    for col in ("s_quantity", "c_balance", "ol_amount"):
+        bad = {c: a.copy() for c, a in fin.items()}
+        nz = np.flatnonzero(bad[col] != db[col])
+        bad[col][nz[len(nz) // 2]] += 1
+        rep = oracle.oe_replay_check(db, bad, W, cap, batch, res, reads, lib=lib)
+        assert not rep["ok"] and rep["bad_columns"] == {col: 1}, (col, rep)
+
+
 def _oe_batch_from_lists(txns):
     n_ops = sum(len(o) for _, o in txns)
     t = np.zeros(len(txns), dtype=wl.TXN_DTYPE)
@@ -329,7 +421,8 @@ PINS = [pin_golden_serial_orders, pin_golden_brute_force, pin_hot_key_prefix_sum
         pin_hot_key_16, pin_read_only_batch, pin_disjoint_order_independent,
         pin_conservation, pin_byte_lanes, pin_replay_accepts_true_order_rejects_swap,
         pin_brute_force_random_tiny, pin_oe_stock_rule_golden, pin_oe_payment_golden,
-        pin_oe_invariants]
+        pin_oe_invariants, pin_oe_consistency_flags_each_violation,
+        pin_oe_replay_rejects_wrong_outcomes]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -388,6 +481,14 @@ MUTANTS = {
     "amount_no_price": ("db->ol_amount[ol] = qty * price;", "db->ol_amount[ol] = qty;"),
     "no_next_o_id": ("db->d_next_o_id[k] += 1;", "db->d_next_o_id[k] += 0;"),
     "remote_ignored": ("db->s_remote_cnt[k] += remote;", "db->s_remote_cnt[k] += 0;"),
+    "consistency_always_ok": ("    return bad;\n}", "    return 0;\n}"),
+    "consistency_no_next_o_id": ("            bad |= 1;", "            bad |= 0;"),
+    "consistency_no_ytd_sum": ("if (s != db->w_ytd[w]) bad |= 2;", "if (s != db->w_ytd[w]) bad |= 0;"),
+    "consistency_no_lines": ("if (present != (l < cnt)) bad |= 4;", "if (present != (l < cnt)) bad |= 0;"),
+    "consistency_lines_off_by_one": ("if (present != (l < cnt)) bad |= 4;",
+                                     "if (present != (l <= cnt)) bad |= 4;"),
+    "oe_insert_wrong_slot": ("uint64_t slot = (uint64_t)dist * db->order_cap + (uint64_t)(o_id - 1);",
+                             "uint64_t slot = (uint64_t)dist * db->order_cap + (uint64_t)o_id;"),
 }
 
 
