@@ -254,7 +254,11 @@ typedef struct gcc_batch gcc_batch;
 
 /* Create a database on desc->device: allocates its tables (zeroed), the
  * per-record concurrency-control words and the scratch needed for batches
- * up to the stated maxima.  Key-value: one table (id 0).  Order-entry: one
+ * up to the stated maxima.  Paper: tables on the GPU are fixed-size arrays
+ * whose size does not change during execution (Sec. III-D, "DBMS Building
+ * Blocks"), and all table data is resident in device memory before any
+ * transaction runs (Sec. IV-A, "Constraints"); one concurrency-control word
+ * per record, as in Table II (Sec. III-E).  Key-value: one table (id 0).  Order-entry: one
  * table per column (ids 0..21 in this order: w_ytd, w_tax, d_ytd, d_tax,
  * d_next_o_id, c_balance, c_ytd_payment, c_payment_cnt, c_discount, i_price,
  * s_quantity, s_ytd, s_order_cnt, s_remote_cnt, o_c_id, o_ol_cnt,
@@ -273,7 +277,11 @@ uint64_t gcc_table_bytes(const gcc_db *db, uint32_t table_id);
 
 /* Copy nbytes (must equal gcc_table_bytes) into table table_id from a host
  * (src_on_device = 0) or device pointer, and reset the concurrency-control
- * words.  Synchronous.  Key-value layout: field-major, slot (key, field) at
+ * words.  Synchronous.  Paper: the host generates the tables and transfers
+ * them to GPU memory before execution (Sec. IV-A, "Experimental Procedure";
+ * the CPU side coordinates data generation and initialisation, Sec. III-B).
+ * Errors: GCC_ERR_INVALID (NULL db or src, bad table id, nbytes differs from
+ * the table's size), GCC_ERR_CUDA.  src stays owned by the caller.  Key-value layout: field-major, slot (key, field) at
  * byte (field * n_records + key) * field_bytes. */
 gcc_status gcc_load_table(gcc_db *db, uint32_t table_id, const void *src,
                           uint64_t nbytes, int src_on_device);
@@ -288,14 +296,27 @@ gcc_status gcc_load_table(gcc_db *db, uint32_t table_id, const void *src,
  * an order-entry database, table_id != 0), GCC_ERR_CUDA. */
 gcc_status gcc_init_table_seeded(gcc_db *db, uint32_t table_id, uint64_t seed);
 
-/* Copy table table_id out (synchronous; waits for prior work on the stream). */
+/* Copy table table_id out (synchronous; waits for prior work on the stream)
+ * to a host (dst_on_device = 0) or device pointer of nbytes (must equal
+ * gcc_table_bytes).  Paper: updates stay in device memory during execution
+ * (Sec. IV-A, "Constraints") and correctness is checked on the host after
+ * execution (Sec. III-D, "Measurements and Verification"); this is the
+ * snapshot such a check compares.  Errors: GCC_ERR_INVALID (NULL pointer,
+ * bad table id, wrong nbytes), GCC_ERR_CUDA.  dst stays owned by the
+ * caller. */
 gcc_status gcc_db_read_table(gcc_db *db, uint32_t table_id, void *dst,
                              uint64_t nbytes, int dst_on_device);
 
 /* Fill *p with the defaults. */
 gcc_status gcc_default_params(gcc_exec_params *p);
 
-/* Submit a batch asynchronously.  txns/ops/operands are host pointers
+/* Submit a batch asynchronously.  Paper: transactions run in batches with
+ * one worker per transaction (Sec. III-B, batch execution model); every
+ * transaction's reads and writes are known before execution, given here as
+ * its op list (Sec. IV-A, "Constraints"); a transaction that fails on a
+ * conflict restarts until it commits (Sec. IV-A, "Experimental Procedure");
+ * every scheme gives serializable results (Sec. III-E).
+ * txns/ops/operands are host pointers
  * (copied before the call returns) or, with inputs_on_device = 1, device
  * pointers that must stay valid until gcc_batch_wait returns.  params may be
  * NULL (defaults).  stream: a cudaStream_t, or NULL for the database's own
@@ -313,7 +334,11 @@ gcc_status gcc_txn_batch_submit(gcc_db *db, gcc_scheme scheme, const gcc_txn *tx
 /* Wait up to timeout_ns (UINT64_MAX = forever) for the batch, then copy its
  * per-transaction results (n_txns entries) and read values (n_ops entries,
  * indexed like ops) to host (outputs_on_device = 0) or device pointers; any
- * output pointer may be NULL.  GCC_ERR_TIMEOUT leaves the batch waitable
+ * output pointer may be NULL.  Paper: the batch is timed from the
+ * initialisation of the scheme to the completion of every transaction, and
+ * the abort rate is aborts per committed transaction (Sec. IV-A, "Metric
+ * Selection"); stats carries both, and per-stage times (Sec. III-D,
+ * "Measurements and Verification").  The outputs stay owned by the caller.  GCC_ERR_TIMEOUT leaves the batch waitable
  * again.  GCC_ERR_DEVICE when stats.device_error is nonzero (outputs are
  * still written). */
 gcc_status gcc_batch_wait(gcc_batch *batch, uint64_t timeout_ns, gcc_txn_result *results,
@@ -517,7 +542,13 @@ gcc_status gcc_autotune(gcc_db *db, gcc_scheme scheme, const gcc_txn *d_txns, ui
  * any stream capture.  Every call reuses the same array, so calls that
  * overlap on the GPU (other streams, other host threads) race with each
  * other.  The call only enqueues work on `stream` (NULL = legacy default
- * stream); per-transaction outcomes land in d_results. */
+ * stream); per-transaction outcomes land in d_results.  Batch-level counters
+ * and device error bits (gcc_batch_stats) stay in the static array and are
+ * not reported: a caller learns of a malformed transaction or a spent wait
+ * budget only from the status of each entry of d_results, so check them all.
+ * Errors: GCC_ERR_CAPACITY (a size above its limit), GCC_ERR_INVALID (bad
+ * slot width, field count, op bound or NULL pointer, or a launch shape that
+ * does not fit an SM), GCC_ERR_CUDA. */
 gcc_status gcc_det_execute_noalloc(void *d_table, uint32_t n_records, uint32_t n_fields,
                                    uint32_t field_bytes, const gcc_txn *d_txns, uint32_t n_txns,
                                    const gcc_op *d_ops, const gcc_operand *d_operands,

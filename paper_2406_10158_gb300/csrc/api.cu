@@ -389,7 +389,10 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
         return GCC_OK;
     }
     if (scheme == GCC_DET && n_ops) {
-        const int bits = std::max(1, kv ? bit_length(db->n_meta - 1) : bit_length(db->n_meta));
+        // records 0..n_meta-1 plus the key n_meta that marks out-of-range
+        // ops: the sort must cover n_meta itself so that those ops sort after
+        // every record's run (a power-of-two n_meta needs one more bit)
+        const int bits = std::max(1, bit_length(db->n_meta));
         GCC_CK(gcc::det_prepare(a, db->sort, db->scan_tmp, bits, db->d.schema, st,
                                 p.det_dataflow == 2));
         launches += 1 + 3 * ((bits + 7) / 8) + 1 + 3 + 1;   // emit, sort, flags, scan, need

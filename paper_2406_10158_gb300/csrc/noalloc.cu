@@ -131,8 +131,10 @@ gcc_status gcc_det_execute_noalloc(void* d_table, uint32_t n_records, uint32_t n
     // preprocessing for every record the batch touches
     e = gcc::launch_batch_begin(a.st, a.dbs, GCC_DET, st);
     if (e == cudaSuccess && n_ops)
+        // the sort covers the key n_records, which marks out-of-range ops, so
+        // that they sort after every record's run
         e = gcc::det_prepare(a, sort, reinterpret_cast<uint32_t*>(base + OFF_SCAN),
-                             bits_for(n_records - 1), GCC_SCHEMA_KV, st);
+                             bits_for(n_records), GCC_SCHEMA_KV, st);
     if (e != cudaSuccess) return na_fail(GCC_ERR_CUDA, cudaGetErrorString(e));
     if (n_txns) {
         const int block = 8 * 32;
@@ -141,7 +143,13 @@ gcc_status gcc_det_execute_noalloc(void* d_table, uint32_t n_records, uint32_t n
         const int occ = gcc::kv_exec_occupancy(GCC_DET, field_bytes, block, smem);
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess || occ <= 0) return na_fail(GCC_ERR_CUDA, "cannot size the launch");
+        if (e != cudaSuccess)
+            return na_fail(GCC_ERR_CUDA, std::string("cannot query the SM count: ") +
+                                             cudaGetErrorString(e));
+        if (occ <= 0)
+            return na_fail(GCC_ERR_INVALID,
+                           "launch shape does not fit an SM (" + std::to_string(block) +
+                               " threads, " + std::to_string(smem) + " B shared)");
         int64_t grid = (int64_t)sms * occ;
         const int64_t needed = ((int64_t)n_txns + slots - 1) / slots;
         if (grid > needed) grid = needed;

@@ -160,6 +160,31 @@ def test_edge_cases(eng, scheme):
         final = db.read_kv()
         assert int(final[1, 5]) == (int(table[1, 5]) + 7) % (1 << 64)
         assert int(reads[5, 0]) == int(table[1, 5])          # op 5: the valid txn's op
+        # an out-of-range key between two valid writers of record 0: with a
+        # power-of-two record count the marker key of out-of-range accesses
+        # (64) must still sort after record 0's accesses, so that the two
+        # writers run in id order and nothing waits on the marker
+        mixed = wl.kv_batch_from_lists([
+            [(0, 0, 1, 5, 0), (9, 1, 0, 0, 0)],
+            [(64, 0, 1, 0, 0), (0, 1, 1, 3, 0)],     # key out of range
+            [(0, 0, 1, 7, 0)],
+            [(9, 1, 1, 11, 0), (0, 1, 0, 0, 0)],
+        ])
+        db.load_kv(table)
+        res, reads, stats = go(eng, db, scheme, mixed, wait_budget_ns=200_000_000)
+        assert res["status"].tolist() == [1, 3, 1, 1], (res, stats)
+        assert stats["timeouts"] == 0
+        final = db.read_kv()
+        rep = oracle.replay_check(table, final, mixed, res, reads, require_all=False)
+        assert rep["ok"] and rep["n_committed"] == 3, rep
+        if scheme.startswith("det"):
+            valid = [0, 2, 3]
+            ref_final, ref_reads = oracle.serial(table, mixed, order=valid)
+            assert np.array_equal(final, ref_final)
+            ops = np.concatenate([np.arange(f, f + n) for f, n in
+                                  zip(mixed.txns["first_op"][valid], mixed.txns["n_ops"][valid])])
+            assert np.array_equal(reads[ops], ref_reads[ops])
+            assert res["commit_order"][valid].tolist() == [0, 1, 2]
         # capacity is enforced on the host
         big = wl.kv_batch(3, nrec=64, nfields=2, n_txns=17, ops_per_txn=2)
         with pytest.raises(eng.GCCError):
