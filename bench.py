@@ -203,11 +203,38 @@ def sector_bytes(batch) -> dict:
     return {"random": random, "stream": stream, "per_txn": (random + stream) / max(1, batch.n_txns)}
 
 
-# DRAM traffic (read + write bytes) of one execute-kernel launch, from the ncu
-# capture in profiles/occ_kv_exec_kernel_full_dram.md: valid only for that
-# kernel build and workload (OCC, default launch, 2^24 x 10 x 16 B, 2^20 txns,
-# Zipf 0.8, read ratio 0.5); None for anything else.
-CAPTURED_TRAFFIC = {("occ", 1 << 24, 1 << 20, 0.8, 0.5, 0, 0): 3.51e9 + 722.34e6}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes) of one
+# execute-kernel launch from an ncu capture, keyed by workload (scheme,
+# records, txns, theta, read ratio, lanes, warps) and stored with the digest
+# of the kernel sources it was taken on: a capture counts only while the
+# sources are unchanged (kernel_sources_digest), and the line reports null
+# otherwise.
+CAPTURED_TRAFFIC = {}
+
+
+def kernel_sources_digest() -> str:
+    """SHA-256 (first 16 hex digits) over the engine's CUDA sources and the
+    public header, in file-name order."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2406_10158_gb300", "csrc", "*.cu*")) +
+                   glob.glob(os.path.join(ROOT, "include", "*.h")))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(key):
+    """The captured DRAM bytes per launch for this workload, or None when
+    there is none or the kernel sources changed since it was taken."""
+    got = CAPTURED_TRAFFIC.get(key)
+    if got is None:
+        return None
+    value, digest = got
+    return value if digest == kernel_sources_digest() else None
 
 
 def replica_totals(dist, committed: float, elapsed: float, device=None):
@@ -252,24 +279,21 @@ def host_info() -> dict:
             "cpu": model or platform.processor() or "unknown"}
 
 
-def time_oracle(table, batch, seconds: float, max_txns=None):
-    """Single-threaded serial execution (the CPU oracle) of a prefix of the
-    batch, repeated until about ``seconds`` have passed; returns txn/s."""
+def time_oracle(table, batch, seconds: float):
+    """Single-threaded serial execution (the CPU oracle) of the whole batch,
+    in transaction-id order, repeated until about ``seconds`` have passed
+    (at least once); returns (txn/s, details).  Each pass continues from the
+    table the previous one left, so every pass does the full batch's work."""
     import oracle
-    from paper_2406_10158_gb300 import workload as wl
-    n = batch.n_txns if max_txns is None else min(batch.n_txns, max_txns)
-    sub = wl.KVBatch(txns=batch.txns[:n], ops=batch.ops, operands=batch.operands)
     work = table.copy()
     done, t_total, reps = 0, 0.0, 0
     while t_total < seconds or reps == 0:
         t0 = time.perf_counter()
-        oracle.serial_inplace(work, sub)
+        oracle.serial_inplace(work, batch)
         t_total += time.perf_counter() - t0
-        done += n
+        done += batch.n_txns
         reps += 1
-        if reps >= 50:
-            break
-    return done / t_total, {"txns": n, "repeats": reps, "seconds": round(t_total, 3)}
+    return done / t_total, {"txns": batch.n_txns, "repeats": reps, "seconds": round(t_total, 3)}
 
 
 # ---------------------------------------------------------------------------
@@ -281,19 +305,19 @@ def run_reference(args, rank, world):
     from paper_2406_10158_gb300 import workload as wl
     table, batch = wl.ycsb_kv(args.seed, theta=args.theta, read_ratio=args.read_ratio,
                               nrec=args.records, n_txns=args.txns)
-    sample = min(batch.n_txns, 1 << 17)
     import oracle
-    sub = wl.KVBatch(txns=batch.txns[:sample], ops=batch.ops, operands=batch.operands)
+    # every step is the whole batch, serially in transaction-id order (the
+    # deterministic scheme's outcome), continuing from the previous step's table
     work = table.copy()
     for _ in range(max(0, args.warmup)):
-        oracle.serial_inplace(work, sub)
+        oracle.serial_inplace(work, batch)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.serial_inplace(work, sub)
+        oracle.serial_inplace(work, batch)
         times.append(time.perf_counter() - t0)
     total = sum(times)
-    value = sample * args.steps / total
+    value = batch.n_txns * args.steps / total
     workload = config_dict(args)
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "txn/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -301,7 +325,7 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": workload,
             "cpu_baseline": {"value": value, "unit": "txn/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {sample} of {batch.n_txns} txns per step, "
+                             "sample": f"the whole batch of {batch.n_txns} txns per step, "
                                        "serial in transaction-id order",
                              "host": host_info()},
             "e2e": {"value": value, "unit": "txn/s", "h2d_bytes_per_step": 0,
@@ -441,8 +465,9 @@ def run_ours(args, rank, world, dist):
     achieved = alg["bytes"] / (kernel_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
-                "traffic": CAPTURED_TRAFFIC.get((args.scheme, args.records, args.txns, args.theta,
-                                                 args.read_ratio, args.lanes, args.warps)),
+                "traffic": captured_traffic((args.scheme, args.records, args.txns, args.theta,
+                                             args.read_ratio, args.lanes, args.warps)),
+                "kernel_sources": kernel_sources_digest(),
                 "kernel": f"kv_exec_kernel<{args.scheme}>", "kernel_ms": round(kernel_ms, 4),
                 "algorithmic_bytes_per_launch": alg["bytes"],
                 "algorithmic_bytes_per_txn": round(alg["per_txn"], 1),
@@ -453,25 +478,42 @@ def run_ours(args, rank, world, dist):
     bound_ms = hot["max_writes"] * probe["occ_cycle_ns"] / 1e6
     sect = sector_bytes(batch)
     sect_gbs = (sect["random"] + sect["stream"]) / (kernel_ms / 1000.0) / 1e9
+    link_ms = hot["max_writes"] * probe["occ_link_ns"] / 1e6
     contention = {
         "bound": "hot-record chain", "hot_record_writes": hot["max_writes"],
         "hot_record_accesses": hot["max_accesses"], "cycle_ns": round(probe["occ_cycle_ns"], 1),
         "cycle_kind": "measured gcc_probe_memory occ_cycle_ns (best over contender counts)",
         "bound_ms": round(bound_ms, 3), "kernel_ms": round(kernel_ms, 4),
-        "frac": round(bound_ms / kernel_ms, 4)}
+        "frac": round(bound_ms / kernel_ms, 4),
+        # second bound: one uncontended link of the engine's own commit
+        # sequence per committed writer of the hottest record
+        "link_ns": round(probe["occ_link_ns"], 1),
+        "link_kind": "measured gcc_probe_memory occ_link_ns (acquire, CAS, acq_rel timestamp, "
+                     "validation load, store, release publish; one thread)",
+        "link_bound_ms": round(link_ms, 3), "link_frac": round(link_ms / kernel_ms, 4)}
+    # L2 atomic throughput the execute kernel achieved, against distinct-word CAS
+    atom_gops = stats["atomics"] / (kernel_ms / 1000.0) / 1e9
+    roofline["atomics"] = {
+        "achieved_gops": round(atom_gops, 4), "peak_gops": round(probe["cas_distinct_gops"], 2),
+        "frac": round(atom_gops / probe["cas_distinct_gops"], 6),
+        "per_batch": stats["atomics"],
+        "peak_kind": "measured gcc_probe_memory cas_distinct_gops",
+        "count_kind": "atomic read-modify-writes issued by the execute kernel (its own counters)"}
     sectors = {
         "bytes_per_txn": round(sect["per_txn"], 1), "achieved_gbs": round(sect_gbs, 1),
         "random_ceiling_gbs": round(probe["gather32_gbs"], 1),
         "random_gbs": round(sect["random"] / (kernel_ms / 1000.0) / 1e9, 1),
         "frac_random": round(sect["random"] / (kernel_ms / 1000.0) / 1e9 / probe["gather32_gbs"], 4),
         "ceiling_kind": "measured gcc_probe_memory gather32_gbs (random 32-byte sector reads)"}
-    probe_out = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in probe.items()}
+    probe_out = {k: (round(v, 3) if isinstance(v, float) else
+                     [round(x, 1) for x in v] if isinstance(v, list) else v)
+                 for k, v in probe.items()}
     cpu = None
     if not args.no_cpu:
-        v, info = time_oracle(table, batch, args.cpu_seconds, max_txns=1 << 18)
+        v, info = time_oracle(table, batch, args.cpu_seconds)
         cpu = {"value": v, "unit": "txn/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {info['txns']} txns of the batch, serial in id order, "
-                         f"{info['repeats']} repeats, {info['seconds']} s",
+               "sample": f"the whole batch of {info['txns']} txns, serial in id order, "
+                         f"{info['repeats']} passes, {info['seconds']} s",
                "host": host_info()}
     out = {"metric": METRIC, "value": value, "unit": "txn/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,

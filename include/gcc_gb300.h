@@ -226,6 +226,11 @@ typedef struct gcc_batch_stats {
     double order_ms;           /* dense commit ranks */
     uint32_t kernel_launches;  /* kernels this execution launched */
     uint32_t grid_blocks;      /* blocks of the execute kernel */
+    uint64_t atomics;          /* global atomic read-modify-write operations the
+                                  execute kernel issued (lock and version CASes,
+                                  timestamp and fetch tickets, counters, queue
+                                  tickets; 0 for the deterministic passes that
+                                  run without it) */
 } gcc_batch_stats;
 
 /* Stage times of one past execution (see gcc_stage_history). */
@@ -569,7 +574,8 @@ typedef struct gcc_memory_probe {
     double l2_load_acquire_ns; /* the same with acquire loads */
     double l2_atomic_ns;       /* dependent atomicAdd(0) on L2-resident words */
     double l2_cas_ns;          /* dependent (failing) 64-bit CAS on L2-resident words */
-    double gather32_gbs;       /* random 32-byte sectors of a 1 GiB buffer, all SMs, GB/s */
+    double gather32_gbs;       /* random 32-byte sectors of a 1 GiB buffer, all SMs,
+                                  GB/s: the best of gather32_by_inflight_gbs */
     double cas_distinct_gops;  /* successful 64-bit CAS, one word per 32 B sector and
                                   thread, all SMs, 1e9 per second */
     double add_same_gops;      /* atomicAdd on one word, one lane per warp, all SMs */
@@ -585,7 +591,19 @@ typedef struct gcc_memory_probe {
     uint32_t contenders;       /* 8 warps per SM (one lane each) */
     uint32_t lock_best_contenders;  /* contending warps at lock_handoff_ns */
     uint32_t occ_best_contenders;   /* contending warps at occ_cycle_ns */
-    uint64_t reserved[2];
+    double fence_ns;           /* fence.acq_rel.gpu with no memory operation in
+                                  flight, one thread */
+    double atomic_acq_rel_ns;  /* dependent acquire-release atomicAdd, one word */
+    double occ_link_ns;        /* one uncontended link of the OCC commit chain as
+                                  the execute kernel runs it (acquire version,
+                                  CAS lock, acquire-release commit timestamp,
+                                  one validation load, value store, release
+                                  publish): the least time per committed
+                                  writer of one record */
+    double gather32_by_inflight_gbs[3]; /* random 32-byte sectors with 4, 8 and
+                                  16 sectors in flight per thread */
+    uint32_t gather32_best_inflight;    /* in-flight count of gather32_gbs */
+    uint32_t reserved;
 } gcc_memory_probe;
 
 /* Run the probes on `device` (about 0.3 s; allocates about 1.5 GiB for the

@@ -412,6 +412,7 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     GCC_CK(cudaEventRecord(rec.ev[1], st));
     if (n_txns && a.rq)
         GCC_CK(cudaMemsetAsync(db->rq, 0, (size_t)gcc::RETRY_QUEUES * 8, st));
+
     if (n_txns) {
         GCC_CK(kv ? gcc::launch_kv_exec(scheme, db->d.field_bytes, a, (int)grid, block, smem, st)
                   : gcc::launch_oe_exec(scheme, a, (int)grid, block, smem, st));
@@ -421,6 +422,10 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     if (n_txns && (scheme == GCC_OCC || scheme == GCC_TO)) {
         GCC_CK(gcc::densify_commit_order(a, db->sort, st));
         launches += 1 + 3 * 4 + 1;                           // emit, 4 sort passes, rank
+    }
+    if (n_txns && scheme == GCC_DET) {
+        GCC_CK(gcc::densify_in_id_order(a, db->fold_flags, db->scan_tmp, st));
+        launches += 1 + 3 + 1;                               // flags, scan, ranks
     }
     if (n_txns && scheme == GCC_TICTOC) {
         GCC_CK(gcc::densify_tictoc(a, db->sort, st));
@@ -471,6 +476,7 @@ void fill_stats(const gcc::BatchState& h, gcc_scheme scheme, uint64_t n_txns,
     s->timeouts = h.timeouts;
     s->invalid = h.invalid;
     s->max_attempts = h.max_attempts;
+    s->atomics = h.atomics;
     s->device_error = h.error;
     s->scheme = scheme;
     if (r && r->used) {

@@ -47,6 +47,7 @@ struct BatchState {
     unsigned long long timeouts;
     unsigned long long invalid;
     unsigned long long max_attempts;
+    unsigned long long atomics;      // global atomic operations of the execute kernel
     unsigned int error;              // GCC_DEVERR_* bits
     unsigned int pad;
 };
@@ -162,14 +163,18 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // One ticket from a counter per calling lane, with one atomic per warp:
-// the lanes active at the call share a single atomicAdd.
+// the lanes active at the call share a single atomicAdd.  *n_atom (when
+// given) counts the atomic on the lane that issues it.
 __device__ __forceinline__ unsigned long long agg_ticket(unsigned long long* ctr,
-                                                        unsigned step = 1) {
+                                                        unsigned step = 1,
+                                                        uint32_t* n_atom = nullptr) {
     unsigned mask = __activemask();
     int leader = __ffs(mask) - 1;
     unsigned long long base = 0;
-    if ((threadIdx.x & 31) == leader)
+    if ((threadIdx.x & 31) == leader) {
         base = atomicAdd(ctr, (unsigned long long)__popc(mask) * step);
+        if (n_atom) ++*n_atom;
+    }
     base = __shfl_sync(mask, base, leader);
     return base + (unsigned long long)__popc(mask & lanemask_lt()) * step;
 }
@@ -177,7 +182,8 @@ __device__ __forceinline__ unsigned long long agg_ticket(unsigned long long* ctr
 // operations are ordered before its ticket and its later ones after it, so a
 // thread whose ticket follows this one (the counter's read-modify-write chain
 // carries the release) also sees everything that preceded this ticket.
-__device__ __forceinline__ unsigned long long agg_ticket_acq_rel(unsigned long long* ctr) {
+__device__ __forceinline__ unsigned long long agg_ticket_acq_rel(unsigned long long* ctr,
+                                                                uint32_t* n_atom = nullptr) {
     unsigned mask = __activemask();
     int leader = __ffs(mask) - 1;
     unsigned long long base = 0;
@@ -185,6 +191,7 @@ __device__ __forceinline__ unsigned long long agg_ticket_acq_rel(unsigned long l
         const unsigned long long inc = (unsigned long long)__popc(mask);
         asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;"
                      : "=l"(base) : "l"(ctr), "l"(inc) : "memory");
+        if (n_atom) ++*n_atom;
     }
     base = __shfl_sync(mask, base, leader);
     return base + (unsigned long long)__popc(mask & lanemask_lt());
@@ -346,6 +353,11 @@ cudaError_t det_fold_kv(const ExecArgs& a, uint32_t field_bytes, SortScratch& s,
 
 // OCC / TO: replace raw commit timestamps by dense ranks 0..committed-1.
 cudaError_t densify_commit_order(const ExecArgs& a, SortScratch& s, cudaStream_t st);
+// Deterministic scheme run op by op: dense ranks in transaction-id order over
+// the committed transactions (`flags`: n_txns words, `scan_tmp`:
+// scan_tmp_words(n_txns) words).
+cudaError_t densify_in_id_order(const ExecArgs& a, uint32_t* flags, uint32_t* scan_tmp,
+                                cudaStream_t st);
 // TicToc: dense ranks in (timestamp, sequence number) order.
 cudaError_t densify_tictoc(const ExecArgs& a, SortScratch& s, cudaStream_t st);
 // Seeded initial values of a key-value table, written on the device.

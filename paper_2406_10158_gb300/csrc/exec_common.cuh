@@ -76,9 +76,11 @@ struct Stage {
 struct Lane {
     uint32_t lane, lig, G, gbase;
     unsigned gmask;
+    mutable uint32_t n_atom = 0;   // global atomic operations this lane issued
 };
 
-enum { ABORT = 0, COMMIT = 1, GIVE_UP = 2 };
+// SKIPPED: DET only, an invalid transaction's accesses were stepped over
+enum { ABORT = 0, COMMIT = 1, GIVE_UP = 2, SKIPPED = 3 };
 
 __device__ __forceinline__ bool collapse_loser(const ExecArgs& a, uint32_t rec) {
     if (a.collapse != 1) return false;
@@ -103,13 +105,13 @@ __device__ __forceinline__ uint32_t group_conflict(const Lane& L, uint32_t frec)
 
 __device__ __forceinline__ unsigned long long group_ticket(const Lane& L, unsigned long long* ctr) {
     unsigned long long v = 0;
-    if (L.lig == 0) v = agg_ticket(ctr);
+    if (L.lig == 0) v = agg_ticket(ctr, 1, &L.n_atom);
     return __shfl_sync(L.gmask, v, L.gbase);
 }
 __device__ __forceinline__ unsigned long long group_ticket_acq_rel(const Lane& L,
                                                                    unsigned long long* ctr) {
     unsigned long long v = 0;
-    if (L.lig == 0) v = agg_ticket_acq_rel(ctr);
+    if (L.lig == 0) v = agg_ticket_acq_rel(ctr, &L.n_atom);
     return __shfl_sync(L.gmask, v, L.gbase);
 }
 
@@ -167,7 +169,7 @@ __device__ int occ_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
         if (j < nops && Work::writes(S.desc[j])) {
             const uint32_t r = Work::rec(a, S.desc[j]);
             bool ok = !collapse_loser(a, r);
-            if (ok) ok = cas64(a.meta + r, S.obs[j], S.obs[j] | OCC_LOCK) == S.obs[j];
+            if (ok) ok = (++L.n_atom, cas64(a.meta + r, S.obs[j], S.obs[j] | OCC_LOCK) == S.obs[j]);
             if (ok) held |= 1ull << k; else { fail = true; frec = r; }
         }
         if (__any_sync(L.gmask, fail)) break;
@@ -254,6 +256,7 @@ __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
                             }
                             fail = true; frec = r; break;
                         }
+                        ++L.n_atom;
                         if (cas64_acquire(m, w, w + TPL_S_ONE) == w) { held |= 1ull << k; break; }
                         if (++tries > a.read_retries) { fail = true; frec = r; break; }
                     }
@@ -261,13 +264,14 @@ __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
                     bool ok = !collapse_loser(a, r);
                     if (ok) {
                         const uint64_t mine = TPL_X | (uint64_t)(t + 1);
+                        ++L.n_atom;
                         uint64_t cur = cas64_acquire(m, 0ull, mine);
                         for (uint32_t waited = 0; WAIT_DIE && cur != 0ull && (cur & TPL_X) &&
                                                   t + 1 < (uint32_t)cur && waited < wait_spins;
                              ++waited) {
                             __nanosleep(64);
                             cur = ld_relaxed(m);
-                            if (cur == 0ull) cur = cas64_acquire(m, 0ull, mine);
+                            if (cur == 0ull) { ++L.n_atom; cur = cas64_acquire(m, 0ull, mine); }
                         }
                         ok = cur == 0ull;
                     }
@@ -300,7 +304,7 @@ __device__ int tpl_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
         if (held >> k & 1) {
             const uint32_t j = L.lig + k * L.G;
             uint64_t* m = a.meta + Work::rec(a, S.desc[j]);
-            if (!Work::writes(S.desc[j])) add64_release(m, (uint64_t)0 - TPL_S_ONE);
+            if (!Work::writes(S.desc[j])) { ++L.n_atom; add64_release(m, (uint64_t)0 - TPL_S_ONE); }
             else st_release(m, 0ull);
         }
     if (fail) crec = group_conflict(L, frec);
@@ -342,6 +346,7 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
                     // raising RTS early only turns away older writers sooner, so
                     // it goes out together with the value load
                     max64(rts_word, ts);
+                    ++L.n_atom;
                     const ulonglong2 v = Work::load(a, d);
                     fence_acq_rel();
                     if (ld_relaxed(wts_word) == y1) { S.oldv[j] = v; break; }
@@ -354,6 +359,7 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
                 for (uint32_t tries = 0; ok; ++tries) {
                     const ulonglong2 w = ld_slot16(m);
                     if ((w.y & TO_DIRTY) || ts < w.x || ts < w.y) { ok = false; break; }
+                    ++L.n_atom;
                     const ulonglong2 o = cas128_acquire(m, w, make_ulonglong2(w.x, TO_DIRTY | ts));
                     if (o.x == w.x && o.y == w.y) { S.obs[j] = w.y; break; }
                     if (tries >= a.read_retries) { ok = false; break; }
@@ -481,6 +487,7 @@ __device__ int tictoc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, 
                 ulonglong2 expect = make_ulonglong2(S.aux[j], S.obs[j]);
                 ok = false;
                 for (uint32_t tries = 0; tries <= a.read_retries; ++tries) {
+                    ++L.n_atom;
                     const ulonglong2 o = cas128_acquire(words + r, expect,
                                                         make_ulonglong2(expect.x, expect.y | TT_LOCK));
                     if (o.x == expect.x && o.y == expect.y) { ok = true; break; }
@@ -511,7 +518,7 @@ __device__ int tictoc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, 
         // the sequence number goes out together with the validation
         __syncwarp(L.gmask);
         unsigned long long sq = 0;
-        if (L.lig == 0) sq = agg_ticket_acq_rel(&a.st->ticket);
+        if (L.lig == 0) sq = agg_ticket_acq_rel(&a.st->ticket, &L.n_atom);
         // validate the read set at the timestamp, extending rts where needed
         for (uint32_t k = 0; k < kmax; ++k) {
             const uint32_t j = L.lig + k * L.G;
@@ -524,6 +531,7 @@ __device__ int tictoc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, 
                     const ulonglong2 w = ld_slot16(m);
                     if (w.y != S.obs[j]) break;                  // written or locked since
                     if (w.x >= ts) { ok = true; break; }
+                    ++L.n_atom;
                     const ulonglong2 o = cas128(m, w, make_ulonglong2(ts, w.y));
                     if (o.x == w.x && o.y == w.y) { ok = true; break; }
                 }
@@ -602,6 +610,7 @@ __device__ int det_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uin
             S.oldv[j] = v;
             if (w) Work::store(a, d, Work::compute(a, d, v, a.operands[first + j]), first + j);
             add64_release(m, w ? DET_WRITE_DONE : DET_READ_DONE);
+            ++L.n_atom;
         }
     }
     if (__any_sync(L.gmask, fail)) return GIVE_UP;
@@ -620,8 +629,10 @@ __device__ void det_skip(const ExecArgs& a, const Lane& L, uint64_t first, uint3
         const uint32_t rec = cc_record(d, Work::SCHEMA, a.n_warehouses, NO_CC);
         if (rec >= a.n_meta) continue;
         const bool w = kind_writes(op_kind(d));
-        if (det_wait(a, a.meta + rec, w || a.det_all, a.need[first + j]))
+        if (det_wait(a, a.meta + rec, w || a.det_all, a.need[first + j])) {
             add64(a.meta + rec, w ? DET_WRITE_DONE : DET_READ_DONE);
+            ++L.n_atom;
+        }
     }
 }
 
@@ -671,7 +682,7 @@ __device__ __forceinline__ uint64_t queue_wait_ns(const ExecArgs& a, uint32_t ah
 // the persistent kernel
 // ---------------------------------------------------------------------------
 struct Counters {
-    unsigned commits = 0, aborts = 0, timeouts = 0, invalid = 0, max_att = 0;
+    unsigned commits = 0, aborts = 0, timeouts = 0, invalid = 0, max_att = 0, atomics = 0;
 };
 
 // Hands out transactions of one batch in id order.
@@ -688,7 +699,7 @@ struct SingleFetch {
     __device__ __forceinline__ bool next(const Lane& L, uint32_t& t, const ExecArgs*& A) {
         if (next_id >= end_id) {
             unsigned long long tt = 0;
-            if (L.lig == 0) tt = agg_ticket(&a->st->fetch, CHUNK);
+            if (L.lig == 0) tt = agg_ticket(&a->st->fetch, CHUNK, &L.n_atom);
             next_id = __shfl_sync(L.gmask, tt, L.gbase);
             end_id = next_id + CHUNK;
         }
@@ -708,6 +719,7 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
     constexpr bool DENSE =
         SCHEME == GCC_NO_WAIT_2PL || SCHEME == GCC_2PL_WAIT_DIE || SCHEME == GCC_DET;
     bool finished = false, has = false, served = false;
+    bool skip = false;            // DET: an invalid transaction's accesses still to advance
     uint32_t t = 0, nops = 0, attempts = 0;
     uint64_t wake = 0;            // global-timer time before which the group waits
     uint32_t qi = NO_Q, qt = 0;   // retry queue and ticket while queued
@@ -745,14 +757,24 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
                     bad = bad || !Work::valid_shape(a, S, nops, tx.type);
                 }
                 if (__any_sync(L.gmask, bad)) {
-                    if constexpr (SCHEME == GCC_DET) det_skip<Work>(a, L, first, nops);
                     if (L.lig == 0) {
                         a.results[t] = gcc_txn_result{GCC_TXN_INVALID, 0u, ~0ull};
                         if (!DENSE) a.order_key[t] = ~0ull;
                         atomicOr(&a.st->error, GCC_DEVERR_INVALID);
                         ++c.invalid;
                     }
-                    F.done(L, a, c);
+                    if constexpr (SCHEME == GCC_DET) {
+                        // its accesses advance their records' counters in the
+                        // attempt step, where the groups they wait for run:
+                        // waiting here, before the warp-wide vote below,
+                        // would hold up a predecessor in the same warp
+                        has = true;
+                        skip = true;
+                        attempts = 0;
+                        wake = 0;
+                    } else {
+                        F.done(L, a, c);
+                    }
                 } else {
                     has = true;
                     attempts = 0;
@@ -780,7 +802,7 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
                 // also tells how many tickets have finished
                 qi = pq;
                 pq = NO_Q;
-                if (L.lig == 0) w = add64(a.rq + qi, 1ull << 32);
+                if (L.lig == 0) { w = add64(a.rq + qi, 1ull << 32); ++L.n_atom; }
                 w = __shfl_sync(L.gmask, w, L.gbase);
                 qt = (uint32_t)(w >> 32);
             } else {
@@ -806,7 +828,10 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
             unsigned long long order_key = 0;
             uint32_t crec = NO_CC, seq = 0;
             int outcome = GIVE_UP;
-            if (go) {
+            if (go && skip) {
+                det_skip<Work>(a, L, first, nops);
+                outcome = SKIPPED;
+            } else if (go) {
                 ++attempts;
                 if constexpr (SCHEME == GCC_OCC)
                     outcome = occ_attempt<Work>(a, L, S, t, first, nops, attempts, order_key, crec);
@@ -826,7 +851,7 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
                 atomicOr(&a.st->error, GCC_DEVERR_DEADLINE);
             }
             if (served) {                      // pass the queue's turn on
-                if (L.lig == 0) add64(a.rq + qi, 1ull);
+                if (L.lig == 0) { add64(a.rq + qi, 1ull); ++L.n_atom; }
                 served = false;
                 qi = NO_Q;
             }
@@ -869,6 +894,7 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
             if (outcome != ABORT) {
                 if (L.lig == 0 && attempts > c.max_att) c.max_att = attempts;
                 has = false;
+                skip = false;
                 F.done(L, a, c);
             }
             __syncwarp(L.gmask);
@@ -912,7 +938,9 @@ __device__ __forceinline__ void flush_counters(BatchState* st, Counters& c) {
     const unsigned timeouts = __reduce_add_sync(0xffffffffu, c.timeouts);
     const unsigned invalid = __reduce_add_sync(0xffffffffu, c.invalid);
     const unsigned max_att = __reduce_max_sync(0xffffffffu, c.max_att);
+    const unsigned atoms = __reduce_add_sync(0xffffffffu, c.atomics);
     if ((threadIdx.x & 31) == 0) {
+        if (atoms) atomicAdd(&st->atomics, (unsigned long long)atoms);
         if (commits) atomicAdd(&st->committed, (unsigned long long)commits);
         if (aborts) atomicAdd(&st->aborts, (unsigned long long)aborts);
         if (timeouts) atomicAdd(&st->timeouts, (unsigned long long)timeouts);
@@ -931,6 +959,7 @@ __global__ void __launch_bounds__(1024) exec_kernel(const __grid_constant__ Exec
     Counters c;
     SingleFetch<SCHEME == GCC_DET ? 1u : 4u> F{&a};
     group_loop<SCHEME, Work>(F, L, S, a.max_ops, deadline, c);
+    c.atomics += L.n_atom;
     flush_counters(a.st, c);
 }
 

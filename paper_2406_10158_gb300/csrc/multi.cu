@@ -65,8 +65,11 @@ struct MultiFetch {
 
     // Counters of the lane-group leader into the batch they belong to.
     __device__ __forceinline__ void flush(const Lane& L) {
+        const uint32_t atoms = __reduce_add_sync(L.gmask, L.n_atom);
+        L.n_atom = 0;
         if (cur && L.lig == 0) {
             BatchState* st = cur->st;
+            if (atoms) atomicAdd(&st->atomics, (unsigned long long)atoms);
             if (c->commits) atomicAdd(&st->committed, (unsigned long long)c->commits);
             if (c->aborts) atomicAdd(&st->aborts, (unsigned long long)c->aborts);
             if (c->timeouts) atomicAdd(&st->timeouts, (unsigned long long)c->timeouts);
@@ -512,6 +515,7 @@ gcc_status gcc_multi_stats(gcc_multi_plan* pl, uint32_t i, gcc_batch_stats* stat
     stats->timeouts = h.timeouts;
     stats->invalid = h.invalid;
     stats->max_attempts = h.max_attempts;
+    stats->atomics = h.atomics;
     stats->device_error = h.error;
     stats->scheme = pl->scheme;
     stats->kernel_launches = pl->launches;

@@ -154,6 +154,10 @@ gcc_status gcc_det_execute_noalloc(void* d_table, uint32_t n_records, uint32_t n
         const int64_t needed = ((int64_t)n_txns + slots - 1) / slots;
         if (grid > needed) grid = needed;
         e = gcc::launch_kv_exec(GCC_DET, field_bytes, a, (int)grid, block, smem, st);
+        // dense ranks over the committed transactions; the sort buffers are
+        // free again once the wait thresholds exist
+        if (e == cudaSuccess)
+            e = gcc::densify_in_id_order(a, sort.k1, reinterpret_cast<uint32_t*>(base + OFF_SCAN), st);
         if (e != cudaSuccess) return na_fail(GCC_ERR_CUDA, cudaGetErrorString(e));
     }
     return GCC_OK;

@@ -292,6 +292,20 @@ __global__ void tt_emit(const gcc_txn_result* __restrict__ res,
     vals[p] = t;
 }
 
+// Deterministic scheme run op by op: every committed transaction's position
+// among the committed ones in id order (an invalid transaction takes none).
+__global__ void id_rank_emit(const gcc_txn_result* __restrict__ res, uint32_t n,
+                             uint32_t* __restrict__ flags) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) flags[t] = res[t].status == GCC_TXN_COMMITTED ? 1u : 0u;
+}
+
+__global__ void id_rank_apply(const uint32_t* __restrict__ before, uint32_t n,
+                              gcc_txn_result* __restrict__ res) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n && res[t].status == GCC_TXN_COMMITTED) res[t].commit_order = before[t];
+}
+
 __global__ void batch_begin_kernel(BatchState* st, DbState* dbs, int scheme) {
     BatchState z{};
     z.ticket_base = scheme == GCC_TO ? dbs->to_clock : dbs->occ_clock;
@@ -376,6 +390,17 @@ cudaError_t densify_tictoc(const ExecArgs& a, SortScratch& s, cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     dense_rank<<<blocks_for(n, 256), 256, 0, st>>>(sk, sv, n, a.results);
+    return cudaGetLastError();
+}
+
+cudaError_t densify_in_id_order(const ExecArgs& a, uint32_t* flags, uint32_t* scan_tmp,
+                                cudaStream_t st) {
+    const uint32_t n = a.n_txns;
+    if (n == 0) return cudaSuccess;
+    id_rank_emit<<<blocks_for(n, 256), 256, 0, st>>>(a.results, n, flags);
+    cudaError_t e = exclusive_scan_u32(flags, n, scan_tmp, st);
+    if (e != cudaSuccess) return e;
+    id_rank_apply<<<blocks_for(n, 256), 256, 0, st>>>(flags, n, a.results);
     return cudaGetLastError();
 }
 

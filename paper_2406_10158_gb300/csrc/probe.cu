@@ -64,23 +64,61 @@ __global__ void add_same_kernel(uint64_t* word, uint32_t iters) {
 }
 
 // Random 32-byte sectors (two 16-byte loads of one sector) of a buffer of
-// `mask` + 1 sectors, four independent sectors in flight per thread.
+// `mask` + 1 sectors, U independent sectors in flight per thread.
+template <int U>
 __global__ void gather32_kernel(const uint8_t* buf, uint64_t mask, uint32_t iters,
                                 uint64_t* sink) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint64_t acc = 0;
-    for (uint32_t k = 0; k < iters; k += 4) {
-        ulonglong2 v[8];
+    for (uint32_t k = 0; k < iters; k += U) {
+        ulonglong2 v[2 * U];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             const uint64_t s = mix64(tid * 0x9E3779B97F4A7C15ull + k + u) & mask;
             v[2 * u] = ld_slot16(buf + s * 32);
             v[2 * u + 1] = ld_slot16(buf + s * 32 + 16);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc += v[u].x ^ v[u].y;
+        for (int u = 0; u < 2 * U; ++u) acc += v[u].x ^ v[u].y;
     }
     if (acc == 0x5a5a5a5a5a5a5a5aull) sink[0] = acc;
+}
+
+// ---- protocol latencies (one thread, L2-resident lines) --------------------
+// mode 0: fence.acq_rel.gpu with nothing outstanding; mode 1: dependent
+// acquire-release atomicAdd on one word; mode 2: one uncontended link of the
+// OCC commit chain as the execute kernel runs it -- acquire the record's
+// version, CAS-lock it, acquire-release commit timestamp, validate one read
+// (relaxed load of another word), write the value, release-store the new
+// version.  A chain of writers of one record cannot commit faster than one
+// such link per writer: each link starts from the previous one's publish.
+__global__ void protocol_kernel(uint64_t* ver, uint64_t* val, uint64_t* other,
+                                unsigned long long* clock, uint32_t steps, int mode,
+                                uint64_t* out) {
+    uint64_t acc = 0;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t s = 0; s < steps; ++s) {
+        if (mode == 0) {
+            fence_acq_rel();
+        } else if (mode == 1) {
+            unsigned long long b;
+            asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;"
+                         : "=l"(b) : "l"(clock), "l"(1ull) : "memory");
+            acc += b;
+        } else {
+            const uint64_t v = ld_acquire(ver);
+            if (cas64(ver, v, v | OCC_LOCK_BIT) != v) { acc += 1; continue; }
+            unsigned long long ts;
+            asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;"
+                         : "=l"(ts) : "l"(clock), "l"(1ull) : "memory");
+            acc += ld_relaxed(other + (ts & 1));
+            st_relaxed(val, ts);
+            st_release(ver, v + 1);
+        }
+    }
+    const uint64_t t1 = globaltimer();
+    out[0] = t1 - t0;
+    out[1] = acc;
 }
 
 // ---- contended single record (one lane per warp, deadline-bounded) --------
@@ -218,16 +256,31 @@ extern "C" gcc_status gcc_probe_memory(int device, gcc_memory_probe* out) {
 
     Ev ev;
     // random 32-byte gathers over the big buffer (also evicts the chains'
-    // lines from L2 before the miss chain)
+    // lines from L2 before the miss chain), 4, 8 and 16 sectors in flight per
+    // thread at full occupancy; the ceiling is the best of the three
     {
         const uint32_t blocks = (uint32_t)sms * 8, iters = 64;
-        gather32_kernel<<<blocks, 256>>>(static_cast<uint8_t*>(big.p), BIG / 32 - 1, 8, res);
-        cudaEventRecord(ev.a);
-        gather32_kernel<<<blocks, 256>>>(static_cast<uint8_t*>(big.p), BIG / 32 - 1, iters, res);
-        cudaEventRecord(ev.b);
-        PROBE_CHECK(cudaEventSynchronize(ev.b));
-        PROBE_CHECK(cudaGetLastError());
-        out->gather32_gbs = (double)blocks * 256 * iters * 32 / (ev.ms() * 1e-3) / 1e9;
+        const uint8_t* b8 = static_cast<uint8_t*>(big.p);
+        const uint64_t mask = BIG / 32 - 1;
+        for (int u = 0; u < 3; ++u) {
+            auto launch = [&](uint32_t it) {
+                if (u == 0) gather32_kernel<4><<<blocks, 256>>>(b8, mask, it, res);
+                else if (u == 1) gather32_kernel<8><<<blocks, 256>>>(b8, mask, it, res);
+                else gather32_kernel<16><<<blocks, 256>>>(b8, mask, it, res);
+            };
+            launch(16);
+            cudaEventRecord(ev.a);
+            launch(iters);
+            cudaEventRecord(ev.b);
+            PROBE_CHECK(cudaEventSynchronize(ev.b));
+            PROBE_CHECK(cudaGetLastError());
+            const double gbs = (double)blocks * 256 * iters * 32 / (ev.ms() * 1e-3) / 1e9;
+            out->gather32_by_inflight_gbs[u] = gbs;
+            if (gbs > out->gather32_gbs) {
+                out->gather32_gbs = gbs;
+                out->gather32_best_inflight = 4u << u;
+            }
+        }
     }
     uint64_t h[2];
     auto chase = [&](uint64_t* buf, uint64_t start, uint32_t steps, int mode,
@@ -247,6 +300,21 @@ extern "C" gcc_status gcc_probe_memory(int device, gcc_memory_probe* out) {
     if ((s = chase(sp, 0, 32768, 1, &out->l2_load_acquire_ns)) != GCC_OK) return s;
     if ((s = chase(sp, 0, 32768, 2, &out->l2_atomic_ns)) != GCC_OK) return s;
     if ((s = chase(sp, 0, 32768, 3, &out->l2_cas_ns)) != GCC_OK) return s;
+
+    // protocol latencies on L2-resident words
+    {
+        uint64_t* ver = m64 + 96;
+        uint64_t* val = m64 + 112;
+        uint64_t* other = m64 + 128;
+        unsigned long long* pclock = reinterpret_cast<unsigned long long*>(m64 + 144);
+        double* dst[3] = {&out->fence_ns, &out->atomic_acq_rel_ns, &out->occ_link_ns};
+        for (int mode = 0; mode < 3; ++mode) {
+            protocol_kernel<<<1, 1>>>(ver, val, other, pclock, 256, mode, res);   // warm
+            protocol_kernel<<<1, 1>>>(ver, val, other, pclock, 4096, mode, res);
+            PROBE_CHECK(cudaMemcpy(h, res, 16, cudaMemcpyDeviceToHost));
+            *dst[mode] = (double)h[0] / 4096;
+        }
+    }
 
     // atomic throughput
     {

@@ -59,7 +59,8 @@ class BatchStats(ctypes.Structure):
                 ("device_error", ctypes.c_uint32), ("scheme", ctypes.c_uint32),
                 ("elapsed_ms", ctypes.c_double), ("prep_ms", ctypes.c_double),
                 ("kernel_ms", ctypes.c_double), ("order_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_uint32), ("grid_blocks", ctypes.c_uint32)]
+                ("kernel_launches", ctypes.c_uint32), ("grid_blocks", ctypes.c_uint32),
+                ("atomics", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -134,7 +135,9 @@ class MemoryProbe(ctypes.Structure):
                 ("occ_cycle_busy_ns", ctypes.c_double),
                 ("sm_count", ctypes.c_uint32), ("contenders", ctypes.c_uint32),
                 ("lock_best_contenders", ctypes.c_uint32), ("occ_best_contenders", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint64 * 2)]
+                ("fence_ns", ctypes.c_double), ("atomic_acq_rel_ns", ctypes.c_double),
+                ("occ_link_ns", ctypes.c_double), ("gather32_by_inflight_gbs", ctypes.c_double * 3),
+                ("gather32_best_inflight", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 COMPLETION_DTYPE = np.dtype([("request", "<u8"), ("lane", "<u4"), ("status", "<u4"),
@@ -341,7 +344,13 @@ def gcc_probe_memory(device: int = 0) -> dict:
     """Memory-system figures of `device` (latencies in ns, rates per second)."""
     m = MemoryProbe()
     _check(load().gcc_probe_memory(device, ctypes.byref(m)))
-    return {k: getattr(m, k) for k, _ in m._fields_ if k != "reserved"}
+    out = {}
+    for k, _ in m._fields_:
+        if k == "reserved":
+            continue
+        v = getattr(m, k)
+        out[k] = list(v) if isinstance(v, ctypes.Array) else v
+    return out
 
 
 def gcc_multi_plan_create(scheme, batches, p: Optional[ExecParams] = None) -> int:

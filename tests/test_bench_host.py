@@ -49,12 +49,25 @@ def test_hot_record_of_a_zipf_batch_matches_its_histogram():
     assert c["max_writes"] <= c["max_accesses"]
 
 
-def test_captured_traffic_only_for_the_captured_workload():
+def test_captured_traffic_only_while_the_kernel_is_unchanged(monkeypatch):
+    """A captured DRAM figure is reported only for its own workload and only
+    while the digest of the kernel sources equals the one it was taken on."""
     key = ("occ", 1 << 24, 1 << 20, 0.8, 0.5, 0, 0)
-    for k in bench.CAPTURED_TRAFFIC:
-        assert k == key
-    assert bench.CAPTURED_TRAFFIC.get(("occ", 1 << 24, 1 << 20, 0.6, 0.5, 0, 0)) is None
-    assert bench.CAPTURED_TRAFFIC.get(("2pl", 1 << 24, 1 << 20, 0.8, 0.5, 0, 0)) is None
+    digest = bench.kernel_sources_digest()
+    assert len(digest) == 16 and digest == bench.kernel_sources_digest()
+    monkeypatch.setattr(bench, "CAPTURED_TRAFFIC", {key: (4.0e9, digest)})
+    assert bench.captured_traffic(key) == 4.0e9
+    assert bench.captured_traffic(("occ", 1 << 24, 1 << 20, 0.6, 0.5, 0, 0)) is None
+    assert bench.captured_traffic(("2pl", 1 << 24, 1 << 20, 0.8, 0.5, 0, 0)) is None
+    monkeypatch.setattr(bench, "CAPTURED_TRAFFIC", {key: (4.0e9, "0" * 16)})
+    assert bench.captured_traffic(key) is None
+
+
+def test_oracle_timing_covers_the_whole_batch():
+    table = wl.kv_table_splitmix(3, 512, 2)
+    b = wl.kv_batch(4, nrec=512, nfields=2, n_txns=300, ops_per_txn=4)
+    v, info = bench.time_oracle(table, b, 0.0)
+    assert info["txns"] == b.n_txns and info["repeats"] == 1 and v > 0
 
 
 def test_host_info_names_cores_and_model():

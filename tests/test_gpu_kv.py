@@ -415,3 +415,4 @@ def test_hot_key_zipf_099(eng, scheme):
         final = db.read_kv()
     assert stats["committed"] == batch.n_txns, stats
     check(table, final, batch, res, reads, scheme, stats)
+
