@@ -28,7 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "committed txns/s + abort rate on 1 GB300 vs plain launch; p99 commit latency"
-SCHEMES = ["occ", "2pl", "2pl_wd", "to", "tictoc", "det"]
+SCHEMES = ["occ", "2pl", "2pl_wd", "to", "tictoc", "mvcc", "det"]
 
 
 def parse_args(argv=None):
@@ -62,6 +62,8 @@ def parse_args(argv=None):
                         "continuous batching of a Poisson trace vs plain per-batch launches; "
                         "sweep: every scheme across the key-value contention levels and the "
                         "order-entry warehouse counts")
+    p.add_argument("--check", action="store_true",
+                   help="sweep: replay every cell's batch on the CPU oracle (slow)")
     p.add_argument("--n-db", type=int, default=64, help="batched form: databases")
     p.add_argument("--rates", default="1e5,1e6,1e7,1e8",
                    help="served form: offered rates (txn/s), comma-separated")
@@ -140,6 +142,17 @@ def algorithmic_bytes(batch) -> dict:
     per_txn = 8 + 16
     total = batch.n_txns * per_txn + n_r * 56 + n_w * 88
     return {"bytes": total, "reads": n_r, "writes": n_w, "per_txn": total / max(1, batch.n_txns)}
+
+
+def mvcc_algorithmic_bytes(batch) -> dict:
+    """algorithmic_bytes plus, per read-modify-write, the version it makes:
+    a 28-byte store entry (timestamp, link, field, 16-byte value) written at
+    commit and read back once when the batch's versions go into the table."""
+    from paper_2406_10158_gb300 import workload as wl
+    base = algorithmic_bytes(batch)
+    n_w = int(np.count_nonzero(batch.ops["kind"] == wl.OP_ADD))
+    total = base["bytes"] + n_w * 2 * 28
+    return {"bytes": total, "per_txn": total / max(1, batch.n_txns)}
 
 
 # Useful bytes of one order-entry op by kind (8-byte descriptor, 16-byte value
@@ -716,6 +729,22 @@ def run_served(args, rank, world):
 # ---------------------------------------------------------------------------
 # contention sweep: every scheme across the key-value and order-entry configs
 # ---------------------------------------------------------------------------
+def replay_kv_cell(db, scheme, batch, tx, op, od, rs, rd, prm) -> bool:
+    """One more execution of a sweep cell's batch, replayed by the CPU oracle
+    from the table it started on (the --check leg: every read value and every
+    word of the final table, bit for bit)."""
+    import torch
+    import oracle
+    from paper_2406_10158_gb300 import workload as wl
+    state = db.read_kv()
+    db.execute(scheme, tx, op, od, batch.n_txns, batch.n_ops, rs, rd, prm)
+    torch.cuda.synchronize()
+    res = rs.cpu().numpy().view(wl.RESULT_DTYPE)
+    reads = rd.cpu().numpy().view(np.uint64).reshape(-1, 2)
+    rep = oracle.replay_check(state, db.read_kv(), batch, res, reads, inplace=True)
+    return bool(rep["ok"])
+
+
 def run_sweep(args, rank, world):
     """Committed txns/s and abort rate of every scheme on the key-value
     workload (2^24 x 10 x 16-byte slots, 2^20 txns x 16 ops) at Zipf theta in
@@ -732,6 +761,14 @@ def run_sweep(args, rank, world):
     torch.cuda.set_device(dev)
     up = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.uint8).reshape(-1)).to(dev)
     prm = eng.params(deadline_ns=int(args.scheme_deadline_s * 1e9))
+    # the deterministic scheme three ways: per-record evaluation (prefix sums
+    # for key-value, one warp per record for order entry), op by op with the
+    # GPUTx waits, and op by op with every access to a record ordered (GaccO)
+    variants = [(s, s, prm) for s in SCHEMES] + [
+        ("det-dataflow", "det", eng.params(deadline_ns=int(args.scheme_deadline_s * 1e9),
+                                           det_dataflow=1)),
+        ("det-gacco", "det", eng.params(deadline_ns=int(args.scheme_deadline_s * 1e9),
+                                        det_dataflow=2))]
 
     def batch_ms(h):
         return h["prep_ms"] + h["kernel_ms"] + h["order_ms"]
@@ -748,19 +785,25 @@ def run_sweep(args, rank, world):
                 rs = torch.empty(batch.n_txns * 16, dtype=torch.uint8, device=dev)
                 rd = torch.empty(batch.n_ops * 16, dtype=torch.uint8, device=dev)
                 torch.cuda.synchronize(dev)
-                useful = algorithmic_bytes(batch)["bytes"]
+                useful0 = algorithmic_bytes(batch)["bytes"]
+                useful_mv = mvcc_algorithmic_bytes(batch)["bytes"]
                 reps = 1 if theta >= 0.99 else 3
-                for scheme in SCHEMES:
+                for name, scheme, p_s in variants:
                     for _ in range(1 + reps):
-                        db.execute(scheme, tx, op, od, batch.n_txns, batch.n_ops, rs, rd, prm)
+                        db.execute(scheme, tx, op, od, batch.n_txns, batch.n_ops, rs, rd, p_s)
                     hist = db.stage_history(reps)
                     st = db.last_stats()
                     ms = statistics.mean(batch_ms(h) for h in hist)
-                    kv_rows.append({"theta": theta, "read_ratio": rr, "scheme": scheme,
-                                    "committed_txn_per_s": st["committed"] / ms * 1e3,
-                                    "abort_rate": st["abort_rate"], "ms_per_batch": ms,
-                                    "algorithmic_gbs": useful / ms / 1e6,
-                                    "all_committed": st["committed"] == batch.n_txns})
+                    useful = useful_mv if scheme == "mvcc" else useful0
+                    row = {"theta": theta, "read_ratio": rr, "scheme": name,
+                           "committed_txn_per_s": st["committed"] / ms * 1e3,
+                           "abort_rate": st["abort_rate"], "ms_per_batch": ms,
+                           "algorithmic_gbs": useful / ms / 1e6,
+                           "all_committed": st["committed"] == batch.n_txns}
+                    if args.check:
+                        row["replayed"] = replay_kv_cell(db, scheme, batch, tx, op, od, rs, rd,
+                                                         p_s)
+                    kv_rows.append(row)
                 db.close()
         for W in (1, 8, 64):
             db0, batch, cap = wl.order_entry(W=W, n_txns=1 << 18)
@@ -770,19 +813,30 @@ def run_sweep(args, rank, world):
             rs = torch.empty(batch.n_txns * 16, dtype=torch.uint8, device=dev)
             rd = torch.empty(batch.n_ops * 16, dtype=torch.uint8, device=dev)
             useful = oe_algorithmic_bytes(batch)["bytes"]
-            for scheme in SCHEMES:
+            for name, scheme, p_s in variants:
+                if scheme == "mvcc":
+                    continue                       # key-value only
                 for _ in range(2):                 # a warm-up batch, then the timed one
                     db.load_oe(db0)               # fresh order slots for the inserts
                     torch.cuda.synchronize(dev)
-                    db.execute(scheme, tx, op, od, batch.n_txns, batch.n_ops, rs, rd, prm)
+                    db.execute(scheme, tx, op, od, batch.n_txns, batch.n_ops, rs, rd, p_s)
                 h = db.stage_history(1)[-1]
                 st = db.last_stats()
                 ms = batch_ms(h)
-                oe_rows.append({"W": W, "scheme": scheme,
-                                "committed_txn_per_s": st["committed"] / ms * 1e3,
-                                "abort_rate": st["abort_rate"], "ms_per_batch": ms,
-                                "algorithmic_gbs": useful / ms / 1e6,
-                                "all_committed": st["committed"] == batch.n_txns})
+                row = {"W": W, "scheme": name,
+                       "committed_txn_per_s": st["committed"] / ms * 1e3,
+                       "abort_rate": st["abort_rate"], "ms_per_batch": ms,
+                       "algorithmic_gbs": useful / ms / 1e6,
+                       "all_committed": st["committed"] == batch.n_txns}
+                if args.check:
+                    import oracle
+                    torch.cuda.synchronize(dev)
+                    res = rs.cpu().numpy().view(wl.RESULT_DTYPE)
+                    reads = rd.cpu().numpy().view(np.uint64).reshape(-1, 2)
+                    rep = oracle.oe_replay_check(db0, db.read_oe(), W, cap, batch, res, reads)
+                    row["replayed"] = bool(rep["ok"]) and oracle.oe_consistency(
+                        db.read_oe(), W, cap) == 0
+                oe_rows.append(row)
             db.close()
     head = next(r for r in kv_rows if r["theta"] == 0.8 and r["read_ratio"] == 0.5
                 and r["scheme"] == "occ")

@@ -56,8 +56,12 @@ typedef enum gcc_scheme {
     GCC_DET = 3,           /* deterministic conflict-ordered batch (GPUTx-like) */
     GCC_TICTOC = 4,        /* OCC with timestamps computed from per-record write
                               and read timestamps (TicToc, Table I) */
-    GCC_2PL_WAIT_DIE = 5   /* two-phase locking, an older transaction waits for a
+    GCC_2PL_WAIT_DIE = 5,  /* two-phase locking, an older transaction waits for a
                               younger exclusive holder, a younger one aborts */
+    GCC_MVCC = 6           /* multi-version timestamp ordering: writes make new
+                              versions, a read takes the newest version older
+                              than its timestamp (Sec. II, Table I; Sec. III-E);
+                              key-value databases */
 } gcc_scheme;
 
 typedef enum gcc_schema {

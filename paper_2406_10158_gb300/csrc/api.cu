@@ -145,6 +145,7 @@ void free_db(gcc_db* db) {
     cudaFree(db->order_key);
     cudaFree(db->fold_flags);
     cudaFree(db->fold_seg);
+    cudaFree(db->mv_slot);
     if (db->h_states) cudaFreeHost(db->h_states);
     for (auto& r : db->stages)
         for (auto& e : r.ev)
@@ -230,6 +231,10 @@ gcc_status create_impl(const gcc_db_desc* desc, gcc_db** out) {
     if (d.schema == GCC_SCHEMA_KV &&
         (s = dev_alloc(&db->fold_seg, gcc::fold_seg_bytes(d.max_batch_ops), "fold carries")))
         return bail(s);
+    // MVCC version pointers, one per slot, zero between batches
+    if (d.schema == GCC_SCHEMA_KV &&
+        (s = dev_alloc(&db->mv_slot, d.n_records * d.n_fields * 4, "version pointers")))
+        return bail(s);
     db->n_h_states = GCC_MAX_OUTSTANDING_BATCHES;
     if (cudaMallocHost(&db->h_states, sizeof(gcc::BatchState) * db->n_h_states) != cudaSuccess)
         return bail(fail(GCC_ERR_NOMEM, "cannot allocate pinned batch states"));
@@ -267,6 +272,7 @@ gcc_status prepare_meta(gcc_db* db, gcc_scheme scheme, cudaStream_t st) {
         case GCC_TICTOC:
             reset = db->meta_state != META_ZERO && db->meta_state != META_TICTOC;
             break;
+        case GCC_MVCC: reset = db->meta_state != META_ZERO; break;   // empty heads
     }
     if (reset) GCC_CK(cudaMemsetAsync(db->meta, 0, db->n_meta * 16, st));
     return GCC_OK;
@@ -277,8 +283,10 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
                         const gcc_exec_params* params, gcc_txn_result* d_results,
                         gcc_operand* d_reads, cudaStream_t stream) {
     if (!db) return fail(GCC_ERR_INVALID, "null database");
-    if ((unsigned)scheme > GCC_2PL_WAIT_DIE)
+    if ((unsigned)scheme > GCC_MVCC)
         return fail(GCC_ERR_INVALID, "unknown scheme %d", (int)scheme);
+    if (scheme == GCC_MVCC && db->d.schema != GCC_SCHEMA_KV)
+        return fail(GCC_ERR_INVALID, "GCC_MVCC runs key-value databases only");
     if (n_txns > db->d.max_batch_txns || n_ops > db->d.max_batch_ops)
         return fail(GCC_ERR_CAPACITY, "batch of %u txns / %llu ops exceeds the database maxima",
                     n_txns, (unsigned long long)n_ops);
@@ -321,7 +329,15 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     a.need = db->need;
     a.order_key = db->order_key;
     a.seq = db->fold_flags;
-    a.order_key_uses_base = scheme == GCC_OCC || scheme == GCC_TO;
+    a.order_key_uses_base = scheme == GCC_OCC || scheme == GCC_TO;   // MVCC: batch-relative
+    // MVCC version store: one entry per committed write, in scratch that
+    // the commit ranks only need after the store has been flattened
+    a.mv_wts = db->sort.k0;
+    a.mv_next = db->sort.v0;
+    a.mv_field = db->sort.k1;
+    a.mv_rec = db->sort.v1;
+    a.mv_val = static_cast<ulonglong2*>(db->fold_seg);
+    a.mv_slot = db->mv_slot;
     a.st = db->st;
     a.dbs = db->dbs;
     a.lanes = p.lanes_per_txn;
@@ -419,7 +435,11 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
         launches += 1;
     }
     GCC_CK(cudaEventRecord(rec.ev[2], st));
-    if (n_txns && (scheme == GCC_OCC || scheme == GCC_TO)) {
+    if (n_txns && scheme == GCC_MVCC) {
+        GCC_CK(gcc::launch_mv_flatten(a, db->d.field_bytes, st));
+        launches += 1;                                       // flatten (+ a memset)
+    }
+    if (n_txns && (scheme == GCC_OCC || scheme == GCC_TO || scheme == GCC_MVCC)) {
         GCC_CK(gcc::densify_commit_order(a, db->sort, st));
         launches += 1 + 3 * 4 + 1;                           // emit, 4 sort passes, rank
     }
@@ -446,6 +466,7 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
         case GCC_TO: db->meta_state = META_TO; break;
         case GCC_DET: db->meta_state = META_DET; break;
         case GCC_TICTOC: db->meta_state = META_TICTOC; break;
+        case GCC_MVCC: db->meta_state = n_txns ? META_ZERO : db->meta_state; break;
     }
     db->last_stream = st;
     db->last_scheme = scheme;

@@ -31,6 +31,18 @@ constexpr uint64_t TO_DIRTY = 1ull << 63;
 // (bit 63).  The record's current version is valid over [wts, rts]; a commit
 // at timestamp c publishes wts = rts = c.
 constexpr uint64_t TT_LOCK = 1ull << 63;
+// MVCC (multi-version TO): one 16-byte head word per record, 32-bit fields
+// with batch-relative timestamps: lo = wts (the record's newest committed
+// version) | rts << 32 (its read timestamp), hi = pending writer's timestamp
+// (0: none; bits 32..63 unused).  Updated only by 128-bit CAS; read by
+// 128-bit loads.  Each (record, field) slot also has a version pointer:
+// index + 1 of its newest entry in the batch's version store (0: the table
+// slot is its only version).
+__host__ __device__ __forceinline__ uint32_t mv_lo(uint64_t w) { return (uint32_t)w; }
+__host__ __device__ __forceinline__ uint32_t mv_hi(uint64_t w) { return (uint32_t)(w >> 32); }
+__host__ __device__ __forceinline__ uint64_t mv_pack(uint32_t lo, uint32_t hi) {
+    return (uint64_t)lo | ((uint64_t)hi << 32);
+}
 // DET: bits 32..63 ops completed on the record, bits 0..31 writes completed,
 // both counted from the record's first position in the batch's sorted
 // access table (Sec. III-E.3, "access tables").
@@ -48,6 +60,7 @@ struct BatchState {
     unsigned long long invalid;
     unsigned long long max_attempts;
     unsigned long long atomics;      // global atomic operations of the execute kernel
+    unsigned long long mv_used;      // MVCC: version-store entries taken
     unsigned int error;              // GCC_DEVERR_* bits
     unsigned int pad;
 };
@@ -90,6 +103,22 @@ __device__ __forceinline__ ulonglong2 ld_slot16(const void* p) {
 __device__ __forceinline__ void st_slot16(void* p, ulonglong2 v) {
     asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};"
                  ::"l"(p), "l"(v.x), "l"(v.y) : "memory");
+}
+// 16-byte load as one 128-bit access, with acquire semantics (a record's
+// MVCC head word: its four fields are read together).
+__device__ __forceinline__ ulonglong2 ld128_acquire(const void* p) {
+    ulonglong2 v;
+    asm volatile(
+        "{\n\t.reg .b128 d;\n\t"
+        "ld.acquire.gpu.global.b128 d, [%2];\n\t"
+        "mov.b128 {%0, %1}, d;\n\t}"
+        : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 // 16-byte compare-and-swap (sm_90 and later): both halves compared and
 // replaced as one atomic operation.
@@ -282,6 +311,14 @@ struct ExecArgs {
     uint32_t queue_turn_ns;     // estimated time per queue turn
     uint32_t queue_width;       // tickets a queue admits at once
     uint32_t queue_after;       // aborts before a transaction uses the queues
+    // MVCC version store of the batch: entry i = (wts, next, record, field,
+    // value); capacity n_ops (one entry per committed write)
+    uint32_t* mv_wts;
+    uint32_t* mv_next;           // index + 1 of the slot's previous entry, 0: none
+    uint32_t* mv_rec;
+    uint32_t* mv_field;
+    ulonglong2* mv_val;
+    uint32_t* mv_slot;           // per slot (field-major): its newest entry + 1
 };
 
 
@@ -360,6 +397,9 @@ cudaError_t densify_in_id_order(const ExecArgs& a, uint32_t* flags, uint32_t* sc
                                 cudaStream_t st);
 // TicToc: dense ranks in (timestamp, sequence number) order.
 cudaError_t densify_tictoc(const ExecArgs& a, SortScratch& s, cudaStream_t st);
+// MVCC, after the execute kernel: every slot's newest entry written into the
+// table, its version pointer cleared, every head word zeroed.
+cudaError_t launch_mv_flatten(const ExecArgs& a, uint32_t field_bytes, cudaStream_t st);
 // Seeded initial values of a key-value table, written on the device.
 cudaError_t launch_seeded_init(uint8_t* table, uint64_t n_records, uint32_t n_fields,
                                uint32_t field_bytes, uint64_t seed, int sm_count,

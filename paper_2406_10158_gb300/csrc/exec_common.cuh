@@ -44,6 +44,9 @@
 //    write and read timestamps instead of a shared clock; a read stays valid
 //    by extending its record's read timestamp (Table I lists TicToc among the
 //    CPU-oriented schemes).  Commit order: (timestamp, sequence number).
+//  * MVCC         -- multi-version TO: writes make versions in a batch store,
+//    a read takes the newest version older than its timestamp (Sec. II,
+//    Sec. III-E "MVCC").  Commit order: the timestamp.
 //  * DET          -- every op waits until the lower-id accesses to its record
 //    that conflict with it are done, then runs; nothing aborts and the outcome
 //    is the serial execution in transaction-id order (Sec. II-C GPUTx;
@@ -565,6 +568,214 @@ __device__ int tictoc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, 
 }
 
 // ---------------------------------------------------------------------------
+// MVCC (multi-version TO)
+// ---------------------------------------------------------------------------
+// The multi-version form of basic TO (Sec. II, "Multi-version Concurrency
+// Control"; Sec. III-E, "MVCC"): every write makes a new immutable version
+// stamped with its writer's timestamp, and a read returns the version whose
+// validity interval holds its timestamp -- the newest version older than it.
+// As in the paper, the latest versions have one array (a version pointer per
+// (record, field) slot) and the history another (the batch's version store:
+// entries taken from one counter, as many as the batch's committed writes, so
+// n_ops entries always suffice, each linked to its slot's previous entry);
+// the table slot is every slot's oldest version and is not written until the
+// batch ends (launch_mv_flatten).  Concurrency control is per record, in the
+// record's head word (engine.cuh): newest version's wts and rts, and a
+// pending writer.
+//  * Write at ts: needs no pending writer, wts < ts and rts <= ts; installs
+//    itself as the pending writer by a CAS and reads its slot's newest
+//    version (the pointer's entry, or the table slot) -- no other writer can
+//    add one while it is pending.
+//  * Read at ts: aborts if an older writer is pending (its version might be
+//    the one to read); if the record's newest version is older than ts it
+//    raises the head's rts to ts by a CAS, so that no writer older than ts can
+//    add a version under it; it then walks its slot's entries from the newest
+//    to the first older than ts (newer ones, from writers after ts, are
+//    stepped over), or takes the table slot.
+//  * Commit: the new entries go into the store, then (release) the slots'
+//    version pointers, then (release) each head is set to (ts, ts, no writer)
+//    by a CAS loop -- only readers' rts raises, all below ts, can move it
+//    meanwhile.  Abort: the pending marks are withdrawn the same way.
+// Versions are stored when the writer commits, so an aborted attempt leaves
+// nothing to undo but its pending marks (the paper's version pointers are
+// likewise updated at commit).  Commit order: the timestamp, batch-relative
+// 32-bit (a batch that would exceed 2^32 - 1 timestamps ends
+// GCC_DEVERR_TS_OVERFLOW).  The protocol was checked against serial replay on
+// interleavings before the kernel existed.
+constexpr uint32_t MV_WALK_MAX = 1u << 16;   // entries a read may step over
+
+__device__ __forceinline__ uint32_t* mv_slot_ptr(const ExecArgs& a, uint64_t d) {
+    return a.mv_slot + (uint64_t)op_field(d) * a.n_records + op_key(d);
+}
+
+// The newest version of op d's slot older than ts: its entries from the
+// newest (version pointer, read with acquire) down, else the table slot.
+// False when the walk would step over more than MV_WALK_MAX entries (the
+// attempt then aborts).
+template <class Work>
+__device__ __forceinline__ bool mv_version(const ExecArgs& a, uint64_t d, uint32_t ts,
+                                           ulonglong2& out) {
+    uint32_t e;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(e) : "l"(mv_slot_ptr(a, d)) : "memory");
+    for (uint32_t n = 0; e != 0; ++n) {
+        if (n >= MV_WALK_MAX) return false;
+        const uint32_t i = e - 1;
+        const uint32_t wts = ld_relaxed_u32(a.mv_wts + i);
+        const uint32_t nxt = ld_relaxed_u32(a.mv_next + i);
+        if (wts < ts) {
+            out = ld_slot16(a.mv_val + i);
+            return true;
+        }
+        e = nxt;
+    }
+    out = Work::load(a, d);
+    return true;
+}
+
+// Withdraw a pending mark (abort) or publish a committed version: a CAS loop
+// that keeps whatever rts raises happened meanwhile.  Only readers move the
+// word while this transaction's mark is on it, each raise at most once per
+// reader attempt, so the loop ends; it is bounded all the same, and a word
+// still not updated after 2^24 tries sets GCC_DEVERR_DEADLINE.
+__device__ __forceinline__ void mv_set_head(const ExecArgs& a, ulonglong2* m, bool commit,
+                                            uint32_t ts, uint32_t& n_atom) {
+    ulonglong2 cur = ld128_acquire(m);
+    for (uint32_t tries = 0;; ++tries) {
+        if (tries >= (1u << 24)) {
+            atomicOr(&a.st->error, GCC_DEVERR_DEADLINE);
+            return;
+        }
+        ulonglong2 nw;
+        if (commit) {
+            const uint32_t rts = mv_hi(cur.x) > ts ? mv_hi(cur.x) : ts;
+            nw = make_ulonglong2(mv_pack(ts, rts), 0ull);
+        } else {
+            nw = make_ulonglong2(cur.x, mv_pack(0u, mv_hi(cur.y)));
+        }
+        ++n_atom;
+        const ulonglong2 o = cas128(m, cur, nw);
+        if (o.x == cur.x && o.y == cur.y) return;
+        cur = o;
+    }
+}
+
+template <class Work>
+__device__ int mvcc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint32_t t,
+                            uint64_t first, uint32_t nops, uint32_t attempt,
+                            unsigned long long& order_key, uint32_t& crec) {
+    const uint32_t kmax = (nops + L.G - 1) / L.G;
+    const unsigned long long t64 = group_ticket(L, &a.st->ticket) + 1;
+    if (t64 >= 0xFFFFFFFFull) {
+        if (L.lig == 0) atomicOr(&a.st->error, GCC_DEVERR_TS_OVERFLOW);
+        return GIVE_UP;
+    }
+    const uint32_t ts = (uint32_t)t64;
+    ulonglong2* heads = reinterpret_cast<ulonglong2*>(a.meta);
+    bool fail = false;
+    uint32_t frec = NO_CC;
+    uint64_t held = 0;               // ops whose record this attempt marked pending
+    for (uint32_t k = 0; k < kmax; ++k) {
+        const uint32_t j = L.lig + k * L.G;
+        if (j < nops) {
+            const uint64_t d = S.desc[j];
+            const uint32_t r = Work::rec(a, d);
+            ulonglong2* m = heads + r;
+            if (!Work::writes(d)) {
+                bool ok = false;
+                for (uint32_t tries = 0; tries <= a.read_retries; ++tries) {
+                    const ulonglong2 h = ld128_acquire(m);
+                    const uint32_t wts = mv_lo(h.x), rts = mv_hi(h.x), pend = mv_lo(h.y);
+                    if (pend != 0 && pend < ts) break;          // an older writer is pending
+                    if (wts < ts && rts < ts) {
+                        ++L.n_atom;
+                        const ulonglong2 o = cas128_acquire(m, h, make_ulonglong2(mv_pack(wts, ts), h.y));
+                        if (o.x != h.x || o.y != h.y) continue;
+                    }
+                    ok = mv_version<Work>(a, d, ts, S.oldv[j]);
+                    break;
+                }
+                if (!ok) { fail = true; frec = r; }
+            } else {
+                bool ok = !collapse_loser(a, r);
+                for (uint32_t tries = 0; ok && tries <= a.read_retries; ++tries) {
+                    const ulonglong2 h = ld128_acquire(m);
+                    const uint32_t wts = mv_lo(h.x), rts = mv_hi(h.x), pend = mv_lo(h.y);
+                    if (pend != 0 || wts >= ts || rts > ts) { ok = false; break; }
+                    ++L.n_atom;
+                    const ulonglong2 o = cas128_acquire(m, h, make_ulonglong2(h.x, mv_pack(ts, mv_hi(h.y))));
+                    if (o.x != h.x || o.y != h.y) {
+                        if (tries == a.read_retries) ok = false;
+                        continue;
+                    }
+                    held |= 1ull << k;
+                    // the slot's newest version: its pointer's entry or the
+                    // table slot (every committed version is older than ts)
+                    uint32_t e;
+                    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(e) : "l"(mv_slot_ptr(a, d)) : "memory");
+                    const ulonglong2 v = e ? ld_slot16(a.mv_val + (e - 1)) : Work::load(a, d);
+                    S.obs[j] = e;                               // the entry it supersedes
+                    S.oldv[j] = v;
+                    S.newv[j] = Work::compute(a, d, v, a.operands[first + j]);
+                    break;
+                }
+                if (!ok) { fail = true; frec = r; }
+            }
+        }
+        if (__any_sync(L.gmask, fail)) break;
+    }
+    fail = __any_sync(L.gmask, fail) || injected_abort(a, t, attempt);
+    if (!fail) {
+        // one range of the version store for the group's writes: lane i's
+        // entries follow those of the lanes before it
+        const uint32_t mine = (uint32_t)__popcll(held);
+        uint32_t incl = mine;                                   // inclusive scan over the group
+        for (uint32_t off = 1; off < L.G; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(L.gmask, incl, off, L.G);
+            if (L.lig >= off) incl += v;
+        }
+        const uint32_t total = __shfl_sync(L.gmask, incl, L.gbase + L.G - 1);
+        unsigned long long base = 0;
+        if (L.lig == 0 && total) { base = atomicAdd(&a.st->mv_used, (unsigned long long)total); ++L.n_atom; }
+        base = __shfl_sync(L.gmask, base, L.gbase);
+        uint32_t e = (uint32_t)base + incl - mine;
+        for (uint32_t k = 0; k < kmax; ++k)
+            if (held >> k & 1) {
+                const uint32_t j = L.lig + k * L.G;
+                const uint64_t d = S.desc[j];
+                a.mv_wts[e] = ts;
+                a.mv_next[e] = (uint32_t)S.obs[j];
+                a.mv_rec[e] = Work::rec(a, d);
+                a.mv_field[e] = op_field(d);
+                st_slot16(a.mv_val + e, S.newv[j]);
+                S.obs[j] = e + 1;                               // the entry it publishes
+                ++e;
+            }
+        if (held) {
+            // the entries before the version pointers that name them, and
+            // the pointers before the heads that admit readers above ts
+            fence_acq_rel();
+            for (uint32_t k = 0; k < kmax; ++k)
+                if (held >> k & 1) {
+                    const uint32_t j = L.lig + k * L.G;
+                    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;"
+                                 ::"l"(mv_slot_ptr(a, S.desc[j])), "r"((uint32_t)S.obs[j]) : "memory");
+                }
+            fence_acq_rel();
+            for (uint32_t k = 0; k < kmax; ++k)
+                if (held >> k & 1)
+                    mv_set_head(a, heads + Work::rec(a, S.desc[L.lig + k * L.G]), true, ts, L.n_atom);
+        }
+        order_key = ts;
+        return COMMIT;
+    }
+    for (uint32_t k = 0; k < kmax; ++k)
+        if (held >> k & 1)
+            mv_set_head(a, heads + Work::rec(a, S.desc[L.lig + k * L.G]), false, ts, L.n_atom);
+    crec = group_conflict(L, frec);
+    return ABORT;
+}
+
+// ---------------------------------------------------------------------------
 // DET
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool det_wait(const ExecArgs& a, uint64_t* m, bool is_write,
@@ -845,6 +1056,9 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
                 else if constexpr (SCHEME == GCC_TICTOC)
                     outcome = tictoc_attempt<Work>(a, L, S, t, first, nops, attempts, order_key,
                                                    seq, crec);
+                else if constexpr (SCHEME == GCC_MVCC)
+                    outcome = mvcc_attempt<Work>(a, L, S, t, first, nops, attempts, order_key,
+                                                 crec);
                 else
                     outcome = det_attempt<Work>(a, L, S, t, first, nops, order_key);
             } else if (L.lig == 0) {

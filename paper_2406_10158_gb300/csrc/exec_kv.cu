@@ -17,6 +17,7 @@ cudaError_t launch_kv_exec(gcc_scheme scheme, uint32_t fb, const ExecArgs& a, in
         GCC_KV_CASE(GCC_DET)
         GCC_KV_CASE(GCC_TICTOC)
         GCC_KV_CASE(GCC_2PL_WAIT_DIE)
+        GCC_KV_CASE(GCC_MVCC)
     }
 #undef GCC_KV_CASE
     return cudaErrorInvalidValue;
@@ -34,6 +35,7 @@ int kv_exec_occupancy(gcc_scheme scheme, uint32_t fb, int block, size_t smem) {
         GCC_KV_OCC(GCC_DET)
         GCC_KV_OCC(GCC_TICTOC)
         GCC_KV_OCC(GCC_2PL_WAIT_DIE)
+        GCC_KV_OCC(GCC_MVCC)
     }
 #undef GCC_KV_OCC
     return 0;

@@ -14,6 +14,7 @@ cudaError_t launch_oe_exec(gcc_scheme scheme, const ExecArgs& a, int grid, int b
         case GCC_DET: return launch_exec<GCC_DET, OeWork>(a, grid, block, smem, s);
         case GCC_TICTOC: return launch_exec<GCC_TICTOC, OeWork>(a, grid, block, smem, s);
         case GCC_2PL_WAIT_DIE: return launch_exec<GCC_2PL_WAIT_DIE, OeWork>(a, grid, block, smem, s);
+        default: break;   // GCC_MVCC: key-value only
     }
     return cudaErrorInvalidValue;
 }
@@ -26,6 +27,7 @@ int oe_exec_occupancy(gcc_scheme scheme, int block, size_t smem) {
         case GCC_DET: return exec_occupancy<GCC_DET, OeWork>(block, smem);
         case GCC_TICTOC: return exec_occupancy<GCC_TICTOC, OeWork>(block, smem);
         case GCC_2PL_WAIT_DIE: return exec_occupancy<GCC_2PL_WAIT_DIE, OeWork>(block, smem);
+        default: break;
     }
     return 0;
 }

@@ -85,7 +85,8 @@ struct gcc_db {
     uint32_t* need = nullptr;
     unsigned long long* order_key = nullptr;
     uint32_t* fold_flags = nullptr;     // deterministic fold: 2 words per transaction
-    void* fold_seg = nullptr;           // deterministic fold: tile carries
+    void* fold_seg = nullptr;           // deterministic fold: tile carries; MVCC values
+    uint32_t* mv_slot = nullptr;        // MVCC: version pointer per key-value slot
     // latest execution
     cudaStream_t last_stream = nullptr;
     gcc_scheme last_scheme = GCC_OCC;

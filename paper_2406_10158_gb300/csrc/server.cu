@@ -330,7 +330,7 @@ gcc_status gcc_server_create(const gcc_server_lane* lanes, uint32_t n, const gcc
         if (!c.db || c.db->d.device != dev) return fail(GCC_ERR_INVALID, "lane %u: bad database", i);
         for (uint32_t j = 0; j < i; ++j)
             if (lanes[j].db == c.db) return fail(GCC_ERR_INVALID, "lane %u: database used twice", i);
-        if (c.scheme > GCC_2PL_WAIT_DIE)
+        if (c.scheme > GCC_MVCC)
             return fail(GCC_ERR_INVALID, "lane %u: unknown scheme", i);
         if (c.max_batch_txns == 0 || c.max_batch_txns > c.db->d.max_batch_txns)
             return fail(GCC_ERR_INVALID, "lane %u: max_batch_txns out of range", i);

@@ -20,8 +20,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libgcc_gb300.so")
 
 SCHEMES = {"2pl": 0, "no_wait_2pl": 0, "to": 1, "occ": 2, "det": 3, "tictoc": 4,
-           "2pl_wd": 5, "wait_die": 5}
-SCHEME_NAMES = {0: "2pl", 1: "to", 2: "occ", 3: "det", 4: "tictoc", 5: "2pl_wd"}
+           "2pl_wd": 5, "wait_die": 5, "mvcc": 6}
+SCHEME_NAMES = {0: "2pl", 1: "to", 2: "occ", 3: "det", 4: "tictoc", 5: "2pl_wd", 6: "mvcc"}
 SCHEMA_KV, SCHEMA_ORDER_ENTRY = 0, 1
 TXN_PENDING, TXN_COMMITTED, TXN_TIMEOUT, TXN_INVALID = 0, 1, 2, 3
 STATUS = {0: "ok", 1: "invalid", 2: "cuda", 3: "timeout", 4: "nomem", 5: "device", 6: "capacity"}

@@ -27,10 +27,11 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a).view(np.uint8).reshape(-1)).cuda()
 
 
-def make_set(eng, n_db=6, seed=3):
+def make_set(eng, n_db=6, seed=3, spec=None):
     import torch
-    spec = wl.batched_kv(seed, n_db=n_db, rec_bits=(10, 14), txn_range=(50, 3000),
-                         ops_range=(4, 64), theta=0.8)
+    if spec is None:
+        spec = wl.batched_kv(seed, n_db=n_db, rec_bits=(10, 14), txn_range=(50, 3000),
+                             ops_range=(4, 64), theta=0.8)
     entries, dbs = [], []
     for (nrec, table, batch) in spec:
         db = eng.Database("kv", n_records=nrec, n_fields=8, field_bytes=8, max_ops_per_txn=64,
@@ -72,6 +73,24 @@ def test_batched_form_replays(eng, scheme):
         plan.launch(use_graph=True)
         states = check_all(eng, plan, dbs, states)
     plan.close()
+    for (db, *_rest) in dbs:
+        db.close()
+
+
+@pytest.mark.slow
+def test_batched_form_full_size(eng):
+    """The batched workload as the benchmark builds it: 64 databases of
+    2^16..2^22 records (log-uniform) x 8 u64 fields, batches of 1,000 ..
+    262,144 txns of 4..64 ops at Zipf 0.8, in one graph-replayed persistent
+    launch per scheme; every database's history replays exactly."""
+    spec = wl.batched_kv(wl.SEEDS[3], n_db=64)
+    entries, dbs = make_set(eng, spec=spec)
+    states = [t for (_, t, _, _, _) in dbs]
+    for scheme in ("occ", "2pl", "to"):
+        plan = eng.MultiPlan(scheme, entries, eng.params(backoff_cap_ns=16_000_000))
+        plan.launch(use_graph=True)
+        states = check_all(eng, plan, dbs, states)
+        plan.close()
     for (db, *_rest) in dbs:
         db.close()
 

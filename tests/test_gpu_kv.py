@@ -12,7 +12,7 @@ import oracle
 from paper_2406_10158_gb300 import workload as wl
 
 pytestmark = pytest.mark.gpu
-SCHEMES = ["occ", "2pl", "2pl_wd", "to", "tictoc", "det", "det-dataflow", "det-gacco"]
+SCHEMES = ["occ", "2pl", "2pl_wd", "to", "tictoc", "mvcc", "det", "det-dataflow", "det-gacco"]
 
 
 # Under heavy contention no-wait locking and timestamp ordering need retry
@@ -243,7 +243,7 @@ def test_outstanding_batch_limit(eng):
         assert np.array_equal(db.read_kv(), state)
 
 
-@pytest.mark.parametrize("scheme", ["occ", "2pl", "2pl_wd", "to", "tictoc"])
+@pytest.mark.parametrize("scheme", ["occ", "2pl", "2pl_wd", "to", "tictoc", "mvcc"])
 def test_injected_aborts_and_backoff(eng, scheme):
     """Forced aborts at the commit point (30%) and randomized backoff exercise
     the retry path; the outcome still replays exactly."""
@@ -268,7 +268,7 @@ def test_attempt_budget_gives_up_cleanly(eng):
     with eng.Database("kv", n_records=1024, n_fields=8, field_bytes=8,
                       max_batch_txns=256) as db:
         db.load_kv(table)
-        for scheme in ("2pl", "2pl_wd", "occ", "to", "tictoc"):
+        for scheme in ("2pl", "2pl_wd", "occ", "to", "tictoc", "mvcc"):
             res, reads, stats = db.run(scheme, batch,
                                        eng.params(inject_abort_ppm=1000000, max_attempts=3))
             assert (res["status"] == oracle.ST_TIMEOUT).all(), scheme
@@ -279,7 +279,7 @@ def test_attempt_budget_gives_up_cleanly(eng):
         check(table, db.read_kv(), batch, res, reads, "2pl", stats)
 
 
-@pytest.mark.parametrize("scheme", ["occ", "2pl", "2pl_wd", "to", "tictoc"])
+@pytest.mark.parametrize("scheme", ["occ", "2pl", "2pl_wd", "to", "tictoc", "mvcc"])
 @pytest.mark.parametrize("policy", [dict(retry_queue=2), dict(queue_after=1),
                                     dict(queue_after=1, queue_width=4),
                                     dict(queue_after=3, queue_turn_ns=200)],
@@ -299,7 +299,7 @@ def test_retry_policies_replay(eng, scheme, policy):
     check(table, final, batch, res, reads, scheme, stats)
 
 
-@pytest.mark.parametrize("scheme", ["occ", "2pl", "2pl_wd", "to", "tictoc"])
+@pytest.mark.parametrize("scheme", ["occ", "2pl", "2pl_wd", "to", "tictoc", "mvcc"])
 def test_retry_queues_after_a_deadline(eng, scheme):
     """A hot batch cut off by a 1 ms kernel deadline while transactions wait in
     retry queues ends with TIMEOUT statuses and the deadline flag; what did
@@ -354,7 +354,8 @@ def test_schemes_share_one_database(eng):
         db.load_kv(state)
         for i, scheme in enumerate(["occ", "occ", "2pl", "det", "to", "occ", "det-dataflow",
                                     "tictoc", "tictoc", "2pl", "2pl_wd", "to", "tictoc",
-                                    "2pl_wd", "det"]):
+                                    "2pl_wd", "det", "mvcc", "mvcc", "occ", "mvcc", "to",
+                                    "mvcc", "det", "mvcc", "2pl"]):
             batch = wl.kv_batch(100 + i, nrec=nrec, nfields=4, n_txns=4096, theta=0.8)
             res, reads, stats = go(eng, db, scheme, batch)
             final = db.read_kv()
@@ -363,12 +364,15 @@ def test_schemes_share_one_database(eng):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("theta", [0.0, 0.8, 0.99])
-def test_ycsb_full_size(eng, theta):
-    """2^24 records x 10 fields in 16-byte slots, 2^20 txns x 16 ops, read
-    ratio 0.5, every scheme in turn on one database, each batch replayed in
-    full by the oracle (the launch shape is the benchmark's)."""
-    table, batch = wl.ycsb_kv(theta=theta, read_ratio=0.5)
+@pytest.mark.parametrize("theta,read_ratio", [(0.0, 0.5), (0.6, 0.5), (0.8, 0.5), (0.99, 0.5),
+                                              (0.6, 0.95), (0.8, 0.95), (0.99, 0.95)])
+def test_ycsb_full_size(eng, theta, read_ratio):
+    """2^24 records x 10 fields in 16-byte slots, 2^20 txns x 16 ops, at the
+    contention levels of the key-value sweep (Zipf 0, 0.6, 0.8, 0.99 at read
+    ratio 0.5; 0.6, 0.8, 0.99 at 0.95): every scheme in turn on one database,
+    each batch replayed in full by the oracle (the launch shape is the
+    benchmark's)."""
+    table, batch = wl.ycsb_kv(theta=theta, read_ratio=read_ratio)
     state = table
     with eng.Database("kv", n_records=1 << 24, n_fields=10, field_bytes=16,
                       max_batch_txns=1 << 20) as db:

@@ -74,6 +74,43 @@ def test_served_mix_replays(eng, schemes):
     assert oracle.oe_consistency(final_oe, W, cap) == 0
 
 
+@pytest.mark.slow
+def test_served_full_size_replays(eng):
+    """The served workload at full size: 2^24 records x 8 u64 fields (Zipf
+    0.8, 80% reads) under OCC on one lane and order entry at W = 8 under
+    basic TO on the other, 2^17 requests 50/50 at 10^7 txn/s offered, the
+    benchmark's batch cap, delay and depth; both lanes' histories replay
+    exactly and the order-entry database stays consistent."""
+    nrec, W, n = 1 << 24, 8, 1 << 17
+    table = wl.kv_table_splitmix(wl.SEEDS[4], nrec, 8)
+    kv = wl.kv_batch(wl.derive_seed(wl.SEEDS[4], 1), nrec=nrec, nfields=8, n_txns=n,
+                     read_ratio=0.8, theta=0.8)
+    oe0, oe, cap = wl.order_entry(seed=wl.SEEDS[4], W=W, n_txns=n)
+    rng = np.random.default_rng(7)
+    lane_of = (rng.random(n) < 0.5).astype(np.uint32)
+    trace = wl.interleave([kv, oe], lane_of)
+    arrivals = wl.poisson_arrivals(wl.SEEDS[4] + 7, n, 1e7)
+    mb = 1 << 14
+    with eng.Database("kv", n_records=nrec, n_fields=8, field_bytes=8, max_batch_txns=mb) as dkv, \
+            eng.Database("oe", n_warehouses=W, order_cap=cap, max_ops_per_txn=33,
+                         max_batch_txns=mb, max_batch_ops=mb * 33) as doe:
+        dkv.load_kv(table)
+        doe.load_oe(oe0)
+        srv = eng.Server([(dkv, "occ", mb, 0, 100_000, 4), (doe, "to", mb, 0, 100_000, 4)],
+                         eng.params(backoff_cap_ns=16_000_000))
+        comp, reads = srv.run_trace(lane_of, trace, arrivals)
+        srv.close()
+        final_kv, final_oe = dkv.read_kv(), doe.read_oe()
+    assert (comp["status"] == oracle.ST_COMMITTED).all()
+    sub, res, rd = lane_history(trace, lane_of, comp, reads, 0)
+    rep = oracle.replay_check(table, final_kv, sub, res, rd)
+    assert rep["ok"], rep
+    sub, res, rd = lane_history(trace, lane_of, comp, reads, 1)
+    rep = oracle.oe_replay_check(oe0, final_oe, W, cap, sub, res, rd)
+    assert rep["ok"], rep
+    assert oracle.oe_consistency(final_oe, W, cap) == 0
+
+
 @pytest.mark.parametrize("scheme", ["occ", "det"])
 def test_served_same_alone_and_in_the_mix(eng, scheme):
     """Requests on disjoint keys: identical reads and final table whether they
