@@ -85,7 +85,17 @@ typedef enum gcc_schema {
  *     (amount = qty * i_price) are inserted.
  *   Payment: W_PAY(w, h) -> (w_ytd, 0); D_PAY(district, h) -> (d_ytd, 0);
  *     C_PAY(customer, h) -> (c_balance, c_payment_cnt), c_balance -= h,
- *     c_ytd_payment += h, c_payment_cnt += 1. */
+ *     c_ytd_payment += h, c_payment_cnt += 1; or, naming the customer by last
+ *     name, C_PAY_BY_NAME(key = the customer's district, aux = last-name id,
+ *     h): among the district's customers with that c_last, ordered by c_first
+ *     and then by customer number, the one at position ceil(n/2) is paid as
+ *     by C_PAY (a name nobody in the district has makes the transaction
+ *     invalid).  The paper's payment names its customer (Sec. IV-A); the
+ *     selection rule is this library's reading.  The lookup uses a
+ *     per-district index sorted by (last, first, number) and binary search
+ *     (the sorted-array index of Sec. III-D), built whenever table 22 or 23
+ *     is loaded, and happens before the transaction touches any control word
+ *     (names are never written). */
 enum gcc_op_kind {
     GCC_OP_READ = 0,
     GCC_OP_ADD = 1,
@@ -96,7 +106,8 @@ enum gcc_op_kind {
     GCC_OE_C_READ = 20,
     GCC_OE_C_PAY = 21,
     GCC_OE_I_READ = 22,
-    GCC_OE_S_NEWORDER = 23
+    GCC_OE_S_NEWORDER = 23,
+    GCC_OE_C_PAY_BY_NAME = 24
 };
 
 enum gcc_txn_type { GCC_TXN_KV = 0, GCC_TXN_NEW_ORDER = 1, GCC_TXN_PAYMENT = 2 };
@@ -128,7 +139,7 @@ typedef struct gcc_op {
     uint32_t key;
     uint8_t field;
     uint8_t kind;
-    uint16_t aux;            /* reserved, 0 */
+    uint16_t aux;            /* C_PAY_BY_NAME: last-name id; otherwise 0 */
 } gcc_op;
 
 /* An op operand or a value read: two 64-bit lanes. */
@@ -271,8 +282,10 @@ typedef struct gcc_batch gcc_batch;
  * table per column (ids 0..21 in this order: w_ytd, w_tax, d_ytd, d_tax,
  * d_next_o_id, c_balance, c_ytd_payment, c_payment_cnt, c_discount, i_price,
  * s_quantity, s_ytd, s_order_cnt, s_remote_cnt, o_c_id, o_ol_cnt,
- * o_all_local, no_flag, ol_i_id, ol_supply_w_id, ol_quantity, ol_amount; all
- * int64; order slot = district * order_cap + o_id - 1, line = slot * 15 + l).
+ * o_all_local, no_flag, ol_i_id, ol_supply_w_id, ol_quantity, ol_amount,
+ * c_last, c_first; all int64; order slot = district * order_cap + o_id - 1,
+ * line = slot * 15 + l; c_last and c_first are the customers' name keys,
+ * read only by payments by last name).
  * Errors: GCC_ERR_INVALID (desc out of range), GCC_ERR_NOMEM, GCC_ERR_CUDA. */
 gcc_status gcc_db_create(const gcc_db_desc *desc, gcc_db **out);
 

@@ -65,7 +65,8 @@ class KV(ctypes.Structure):
 OE_COLUMNS = ["w_ytd", "w_tax", "d_ytd", "d_tax", "d_next_o_id", "c_balance",
               "c_ytd_payment", "c_payment_cnt", "c_discount", "i_price", "s_quantity",
               "s_ytd", "s_order_cnt", "s_remote_cnt", "o_c_id", "o_ol_cnt", "o_all_local",
-              "no_flag", "ol_i_id", "ol_supply_w_id", "ol_quantity", "ol_amount"]
+              "no_flag", "ol_i_id", "ol_supply_w_id", "ol_quantity", "ol_amount",
+              "c_last", "c_first"]
 
 
 class OE(ctypes.Structure):

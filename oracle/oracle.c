@@ -255,8 +255,38 @@ void orc_kv_sum(const orc_kv *db, uint64_t out[2])
 /*   1 D_PAY  key district operand h   reads (d_ytd, 0);  d_ytd += h         */
 /*   2 C_PAY  key customer operand h   reads (c_balance, c_payment_cnt);     */
 /*        c_balance -= h; c_ytd_payment += h; c_payment_cnt += 1             */
+/*     or C_PAY_BY_NAME key district, aux last-name id, operand h: the       */
+/*        customer of that district chosen by name (oe_customer_by_name),    */
+/*        then as C_PAY                                                      */
 /* ------------------------------------------------------------------------ */
 enum { OE_ITEMS = 100000, OE_CUST = 3000, OE_DIST = 10, OE_LINES = 15 };
+
+/* Payment by last name: among the district's customers whose last name is
+ * `name`, ordered by first name and then by customer index, the one at
+ * position ceil(n/2) (1-based).  Returns the customer's row, or -1 when
+ * nobody in the district has the name.  (The paper names the payment
+ * transaction only, Sec. IV-A; this selection rule is the library's reading.) */
+static int64_t oe_customer_by_name(const orc_oe *db, uint64_t district, int64_t name)
+{
+    uint64_t base = district * OE_CUST;
+    int64_t n = 0;
+    for (uint64_t c = 0; c < OE_CUST; c++)
+        if (db->c_last[base + c] == name) n++;
+    if (n == 0) return -1;
+    int64_t want = (n + 1) / 2 - 1;          /* 0-based position of ceil(n/2) */
+    for (uint64_t c = 0; c < OE_CUST; c++) {
+        if (db->c_last[base + c] != name) continue;
+        int64_t before = 0;                  /* named customers ordered before c */
+        for (uint64_t o = 0; o < OE_CUST; o++) {
+            if (db->c_last[base + o] != name) continue;
+            if (db->c_first[base + o] < db->c_first[base + c] ||
+                (db->c_first[base + o] == db->c_first[base + c] && o < c))
+                before++;
+        }
+        if (before == want) return (int64_t)(base + c);
+    }
+    return -1;
+}
 
 static int oe_apply_op(orc_oe *db, const orc_op *op, const uint64_t *operand,
                        uint64_t out[2])
@@ -290,7 +320,14 @@ static int oe_apply_op(orc_oe *db, const orc_op *op, const uint64_t *operand,
         out[0] = (uint64_t)db->c_discount[k];
         out[1] = (uint64_t)db->c_balance[k];
         return ORC_OK;
+    case ORC_OE_C_PAY_BY_NAME:
     case ORC_OE_C_PAY: {
+        if (op->kind == ORC_OE_C_PAY_BY_NAME) {
+            if (k >= W * OE_DIST) return ORC_BAD_KEY;
+            int64_t row = oe_customer_by_name(db, k, (int64_t)op->aux);
+            if (row < 0) return ORC_BAD_KEY;
+            k = (uint32_t)row;
+        }
         if (k >= W * OE_DIST * OE_CUST) return ORC_BAD_KEY;
         int64_t h = (int64_t)operand[0];
         out[0] = (uint64_t)db->c_balance[k];
@@ -374,7 +411,8 @@ int orc_oe_run_txn(orc_oe *db, const orc_txn *t, const orc_op *ops,
                 return ORC_BAD_KIND;
     } else if (t->type == ORC_TXN_PAYMENT) {
         if (t->n_ops != 3 || ops[f].kind != ORC_OE_W_PAY ||
-            ops[f + 1].kind != ORC_OE_D_PAY || ops[f + 2].kind != ORC_OE_C_PAY)
+            ops[f + 1].kind != ORC_OE_D_PAY ||
+            (ops[f + 2].kind != ORC_OE_C_PAY && ops[f + 2].kind != ORC_OE_C_PAY_BY_NAME))
             return ORC_BAD_KIND;
     } else {
         return ORC_BAD_TYPE;

@@ -48,7 +48,7 @@ enum { ORC_READ = 0, ORC_ADD = 1,
        /* order-entry op kinds */
        ORC_OE_W_READ = 16, ORC_OE_W_PAY = 17, ORC_OE_D_NEWORDER = 18,
        ORC_OE_D_PAY = 19, ORC_OE_C_READ = 20, ORC_OE_C_PAY = 21,
-       ORC_OE_I_READ = 22, ORC_OE_S_NEWORDER = 23 };
+       ORC_OE_I_READ = 22, ORC_OE_S_NEWORDER = 23, ORC_OE_C_PAY_BY_NAME = 24 };
 
 /* transaction types */
 enum { ORC_TXN_KV = 0, ORC_TXN_NEW_ORDER = 1, ORC_TXN_PAYMENT = 2 };
@@ -139,6 +139,8 @@ typedef struct {
     int64_t *no_flag;
     /* order-line [10W * order_cap * 15] */
     int64_t *ol_i_id, *ol_supply_w_id, *ol_quantity, *ol_amount;
+    /* customer names [30000W], never written: last-name id, first-name key */
+    int64_t *c_last, *c_first;
 } orc_oe;
 
 int orc_oe_run_txn(orc_oe *db, const orc_txn *t, const orc_op *ops,

@@ -146,6 +146,9 @@ void free_db(gcc_db* db) {
     cudaFree(db->fold_flags);
     cudaFree(db->fold_seg);
     cudaFree(db->mv_slot);
+    cudaFree(db->name_idx);
+    cudaFree(db->name_last);
+    cudaFree(db->ops_resolved);
     if (db->h_states) cudaFreeHost(db->h_states);
     for (auto& r : db->stages)
         for (auto& e : r.ev)
@@ -209,6 +212,15 @@ gcc_status create_impl(const gcc_db_desc* desc, gcc_db** out) {
             cudaSuccess)
             return bail(fail(GCC_ERR_CUDA, "cannot upload column table"));
         db->n_meta = W * (1 + OE_DIST + OE_DIST * OE_CUST) + W * OE_ITEMS;
+        const uint64_t n_cust = W * OE_DIST * OE_CUST;
+        if ((s = dev_alloc(&db->name_idx, n_cust * 4, "last-name index"))) return bail(s);
+        if ((s = dev_alloc(&db->name_last, n_cust * 8, "last-name index"))) return bail(s);
+        if ((s = dev_alloc(&db->ops_resolved, d.max_batch_ops * 8, "resolved ops"))) return bail(s);
+        if (gcc::build_name_index(db->cols[gcc::rt::OE_C_LAST], db->cols[gcc::rt::OE_C_FIRST],
+                                  (uint32_t)(W * OE_DIST), db->name_idx, db->name_last,
+                                  db->stream) != cudaSuccess ||
+            cudaStreamSynchronize(db->stream) != cudaSuccess)
+            return bail(fail(GCC_ERR_CUDA, "cannot build the last-name index"));
     }
     if ((s = dev_alloc(&db->meta, db->n_meta * 16, "control words (16 bytes per record for TO)"))) return bail(s);
     if ((s = dev_alloc(&db->st, sizeof(gcc::BatchState), "batch state"))) return bail(s);
@@ -361,6 +373,14 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
     GCC_CK(gcc::launch_batch_begin(db->st, db->dbs, scheme, st));
     launches += 1;
     const bool kv = db->d.schema == GCC_SCHEMA_KV;
+    if (!kv && n_ops) {
+        // payments by last name become payments of the customer they name,
+        // before any scheme sees the batch
+        GCC_CK(gcc::resolve_by_name(a.ops, n_ops, db->d.n_warehouses, db->name_idx, db->name_last,
+                                    db->ops_resolved, st));
+        a.ops = db->ops_resolved;
+        launches += 1;
+    }
     // deterministic key-value batches: every record chain by prefix sums
     const bool fold = scheme == GCC_DET && kv && !p.det_dataflow;
     if (fold) {
@@ -565,6 +585,11 @@ gcc_status gcc_load_table(gcc_db* db, uint32_t id, const void* src, uint64_t nby
                       src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
     GCC_CK(cudaMemset(db->meta, 0, db->n_meta * 16));
     db->meta_state = META_ZERO;
+    if (db->d.schema == GCC_SCHEMA_ORDER_ENTRY &&
+        (id == (uint32_t)gcc::rt::OE_C_LAST || id == (uint32_t)gcc::rt::OE_C_FIRST))
+        GCC_CK(gcc::build_name_index(db->cols[gcc::rt::OE_C_LAST], db->cols[gcc::rt::OE_C_FIRST],
+                                     db->d.n_warehouses * gcc::rt::OE_DIST, db->name_idx,
+                                     db->name_last, nullptr));
     GCC_CK(cudaDeviceSynchronize());
     return GCC_OK;
 }

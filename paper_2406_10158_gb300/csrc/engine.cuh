@@ -242,6 +242,7 @@ __host__ __device__ __forceinline__ bool kind_writes(uint32_t kind) {
         case GCC_OE_D_PAY:
         case GCC_OE_C_PAY:
         case GCC_OE_S_NEWORDER:
+        case GCC_OE_C_PAY_BY_NAME:
             return true;
         default:
             return false;
@@ -397,6 +398,16 @@ cudaError_t densify_in_id_order(const ExecArgs& a, uint32_t* flags, uint32_t* sc
                                 cudaStream_t st);
 // TicToc: dense ranks in (timestamp, sequence number) order.
 cudaError_t densify_tictoc(const ExecArgs& a, SortScratch& s, cudaStream_t st);
+// Payment by last name: per-district index of the customers in (last name,
+// first name, index) order (idx: customer numbers, last_sorted: their last
+// names; 3000 entries per district), and the batch's ops with every by-name
+// payment op replaced by a payment of the customer it names (or by an op of
+// unknown kind, which makes its transaction invalid, when nobody has the
+// name).
+cudaError_t build_name_index(const int64_t* c_last, const int64_t* c_first, uint32_t n_districts,
+                             uint32_t* idx, int64_t* last_sorted, cudaStream_t st);
+cudaError_t resolve_by_name(const uint64_t* ops, uint64_t n, uint32_t W, const uint32_t* idx,
+                            const int64_t* last_sorted, uint64_t* out, cudaStream_t st);
 // MVCC, after the execute kernel: every slot's newest entry written into the
 // table, its version pointer cleared, every head word zeroed.
 cudaError_t launch_mv_flatten(const ExecArgs& a, uint32_t field_bytes, cudaStream_t st);

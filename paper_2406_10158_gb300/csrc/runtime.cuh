@@ -10,7 +10,8 @@
 namespace gcc {
 namespace rt {
 
-constexpr int OE_NCOLS = 22;
+constexpr int OE_NCOLS = 24;
+constexpr int OE_C_LAST = 22, OE_C_FIRST = 23;
 constexpr uint32_t OE_ITEMS = 100000, OE_DIST = 10, OE_CUST = 3000, OE_LINES = 15;
 
 // Rows of each order-entry column, in table-id order.
@@ -22,7 +23,8 @@ inline uint64_t oe_rows(uint32_t col, uint64_t W, uint64_t cap) {
     if (col < 10) return OE_ITEMS;                  // i_price
     if (col < 14) return W * OE_ITEMS;              // s_*
     if (col < 18) return nd * cap;                  // o_*, no_flag
-    return nd * cap * OE_LINES;                     // ol_*
+    if (col < 22) return nd * cap * OE_LINES;       // ol_*
+    return nd * OE_CUST;                            // c_last, c_first
 }
 
 enum MetaState { META_ZERO, META_OCC, META_TO, META_DET, META_TICTOC, META_UNKNOWN };
@@ -87,6 +89,11 @@ struct gcc_db {
     uint32_t* fold_flags = nullptr;     // deterministic fold: 2 words per transaction
     void* fold_seg = nullptr;           // deterministic fold: tile carries; MVCC values
     uint32_t* mv_slot = nullptr;        // MVCC: version pointer per key-value slot
+    // order-entry: customers by (last, first, number) per district, and the
+    // batch's ops with by-name payments resolved
+    uint32_t* name_idx = nullptr;
+    int64_t* name_last = nullptr;
+    uint64_t* ops_resolved = nullptr;
     // latest execution
     cudaStream_t last_stream = nullptr;
     gcc_scheme last_scheme = GCC_OCC;

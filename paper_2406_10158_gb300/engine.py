@@ -385,7 +385,7 @@ def gcc_last_error() -> str:
 # ---------------------------------------------------------------------------
 class Database:
     """A device-resident database: key-value (one field-major table) or
-    order-entry (22 int64 column tables)."""
+    order-entry (24 int64 column tables)."""
 
     def __init__(self, schema: str = "kv", *, n_records: int = 0, n_fields: int = 0,
                  field_bytes: int = 8, n_warehouses: int = 0, order_cap: int = 0,

@@ -337,6 +337,7 @@ def ycsb_kv(seed: int = SEEDS[1], *, theta: float = 0.8, read_ratio: float = 0.5
 # op kinds (values fixed by the C ABI)
 OE_W_READ, OE_W_PAY, OE_D_NEWORDER, OE_D_PAY = 16, 17, 18, 19
 OE_C_READ, OE_C_PAY, OE_I_READ, OE_S_NEWORDER = 20, 21, 22, 23
+OE_C_PAY_BY_NAME = 24
 
 OE_DISTRICTS = 10
 OE_CUSTOMERS = 3000
@@ -347,7 +348,8 @@ OE_INITIAL_ORDERS = 3000
 OE_COLUMNS = ("w_ytd", "w_tax", "d_ytd", "d_tax", "d_next_o_id", "c_balance",
               "c_ytd_payment", "c_payment_cnt", "c_discount", "i_price", "s_quantity",
               "s_ytd", "s_order_cnt", "s_remote_cnt", "o_c_id", "o_ol_cnt", "o_all_local",
-              "no_flag", "ol_i_id", "ol_supply_w_id", "ol_quantity", "ol_amount")
+              "no_flag", "ol_i_id", "ol_supply_w_id", "ol_quantity", "ol_amount",
+              "c_last", "c_first")
 
 
 def oe_column_rows(W: int, order_cap: int) -> dict:
@@ -414,6 +416,9 @@ def oe_initial_db(seed: int, W: int, order_cap: int) -> dict:
     db["c_discount"][:] = rng.integers(0, 5001, size=n_c)
     db["i_price"][:] = rng.integers(100, 10_001, size=OE_ITEMS)
     db["s_quantity"][:] = rng.integers(10, 101, size=W * OE_ITEMS)
+    names = oe_customer_names(seed, W)               # its own stream
+    db["c_last"][:] = names["c_last"]
+    db["c_first"][:] = names["c_first"]
     # initial orders
     o = np.arange(OE_INITIAL_ORDERS)
     slots = (np.arange(n_d)[:, None] * order_cap + o[None, :]).ravel()
@@ -436,7 +441,8 @@ def oe_initial_db(seed: int, W: int, order_cap: int) -> dict:
 
 
 def oe_batch(seed: int, W: int, n_txns: int, new_order_frac: float = 0.5,
-             remote_line_frac: float = 0.01, remote_customer_frac: float = 0.15) -> KVBatch:
+             remote_line_frac: float = 0.01, remote_customer_frac: float = 0.15,
+             by_name_frac: float = 0.0) -> KVBatch:
     """A mix of NewOrder and Payment transactions encoded as op lists (layout
     documented with the order-entry op kinds in the C ABI header).
 
@@ -444,7 +450,12 @@ def oe_batch(seed: int, W: int, n_txns: int, new_order_frac: float = 0.5,
     lines with distinct NURand(8191) items, quantity 1-10, each line supplied
     by another warehouse with probability ``remote_line_frac`` when W > 1.
     Payment: amount uniform in [100, 500000] cents; the customer belongs to
-    another warehouse with probability ``remote_customer_frac`` when W > 1."""
+    another warehouse with probability ``remote_customer_frac`` when W > 1,
+    and is named by last name (op OE_C_PAY_BY_NAME: key = the customer's
+    district, aux = a NURand(255, 0, 999) last-name id) with probability
+    ``by_name_frac`` (TPC-C's share is 60%), else by id.  The by-name draws
+    come after all others, so by_name_frac = 0 gives the same batch as
+    before the option existed."""
     rng = np.random.Generator(np.random.PCG64(derive_seed(seed, 31)))
     c_item = int(rng.integers(0, 8192))
     c_cust = int(rng.integers(0, 1024))
@@ -518,6 +529,14 @@ def oe_batch(seed: int, W: int, n_txns: int, new_order_frac: float = 0.5,
     ops["key"][f_p + 2] = (c_w * OE_DISTRICTS + c_d) * OE_CUSTOMERS + c_pay
     for k in range(3):
         operands[f_p + k, 0] = h
+    if by_name_frac > 0 and n_pay:
+        by_name = rng.random(n_pay) < by_name_frac
+        c_run = int(rng.integers(0, 256))
+        name = nurand(rng, 255, 0, OE_LAST_NAMES - 1, c_run, n_pay)
+        pos = f_p[by_name] + 2
+        ops["kind"][pos] = OE_C_PAY_BY_NAME
+        ops["key"][pos] = (c_w * OE_DISTRICTS + c_d)[by_name]
+        ops["aux"][pos] = name[by_name]
     return KVBatch(txns=txns, ops=ops, operands=operands)
 
 
@@ -532,9 +551,10 @@ def oe_order_cap(batches, W: int, margin: int = 16) -> int:
     return int(OE_INITIAL_ORDERS + per.max() + margin) if per.size else OE_INITIAL_ORDERS
 
 
-def order_entry(seed: int = SEEDS[2], W: int = 8, n_txns: int = 1 << 18, order_cap=None):
+def order_entry(seed: int = SEEDS[2], W: int = 8, n_txns: int = 1 << 18, order_cap=None,
+                by_name_frac: float = 0.0):
     """Initial database, batch and order capacity for the order-entry mix."""
-    batch = oe_batch(derive_seed(seed, 40 + W), W, n_txns)
+    batch = oe_batch(derive_seed(seed, 40 + W), W, n_txns, by_name_frac=by_name_frac)
     cap = order_cap or oe_order_cap([batch], W)
     return oe_initial_db(seed, W, cap), batch, cap
 

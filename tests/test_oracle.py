@@ -402,6 +402,34 @@ def pin_oe_replay_rejects_wrong_outcomes(lib):
         assert not rep["ok"] and rep["bad_columns"] == {col: 1}, (col, rep)
 
 
+def pin_oe_payment_by_name_golden(lib):
+    """A payment by last name in district 0 lands on the customer the
+    hand-worked fixture selects (the middle one by first name, then index),
+    and a name nobody has is refused."""
+    g = _golden("oe_last_name.json")
+    W, cap, db = _tiny_oe(lib)
+    db["c_last"][:] = 500                          # nobody else has a fixture name
+    n = len(g["c_last"])
+    db["c_last"][:n] = g["c_last"]
+    db["c_first"][:n] = g["c_first"]
+    for name, want in g["expected"].items():
+        batch = _oe_batch_from_lists([(wl.TXN_PAYMENT, [(0, wl.OE_W_PAY, 700, 0),
+                                                         (0, wl.OE_D_PAY, 700, 0),
+                                                         (0, wl.OE_C_PAY_BY_NAME, 700, 0)])])
+        batch.ops["aux"][2] = int(name)
+        if want < 0:
+            with pytest.raises(oracle.OracleError):
+                oracle.oe_serial(db, W, cap, batch, lib=lib)
+            continue
+        fin, reads = oracle.oe_serial(db, W, cap, batch, lib=lib)
+        changed = np.flatnonzero(fin["c_balance"] != db["c_balance"])
+        assert changed.tolist() == [want], (name, changed)
+        assert fin["c_balance"][want] == db["c_balance"][want] - 700
+        assert fin["c_payment_cnt"][want] == db["c_payment_cnt"][want] + 1
+        assert reads[2].view(np.int64).tolist() == [int(db["c_balance"][want]),
+                                                     int(db["c_payment_cnt"][want])]
+
+
 def _oe_batch_from_lists(txns):
     n_ops = sum(len(o) for _, o in txns)
     t = np.zeros(len(txns), dtype=wl.TXN_DTYPE)
@@ -422,7 +450,7 @@ PINS = [pin_golden_serial_orders, pin_golden_brute_force, pin_hot_key_prefix_sum
         pin_conservation, pin_byte_lanes, pin_replay_accepts_true_order_rejects_swap,
         pin_brute_force_random_tiny, pin_oe_stock_rule_golden, pin_oe_payment_golden,
         pin_oe_invariants, pin_oe_consistency_flags_each_violation,
-        pin_oe_replay_rejects_wrong_outcomes]
+        pin_oe_replay_rejects_wrong_outcomes, pin_oe_payment_by_name_golden]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -487,6 +515,11 @@ MUTANTS = {
     "consistency_no_lines": ("if (present != (l < cnt)) bad |= 4;", "if (present != (l < cnt)) bad |= 0;"),
     "consistency_lines_off_by_one": ("if (present != (l < cnt)) bad |= 4;",
                                      "if (present != (l <= cnt)) bad |= 4;"),
+    "by_name_upper_middle": ("int64_t want = (n + 1) / 2 - 1;", "int64_t want = n / 2;"),
+    "by_name_ties_descending": ("(db->c_first[base + o] == db->c_first[base + c] && o < c))",
+                                "(db->c_first[base + o] == db->c_first[base + c] && o > c))"),
+    "by_name_ignores_first": ("if (db->c_first[base + o] < db->c_first[base + c] ||",
+                              "if (0 ||"),
     "oe_insert_wrong_slot": ("uint64_t slot = (uint64_t)dist * db->order_cap + (uint64_t)(o_id - 1);",
                              "uint64_t slot = (uint64_t)dist * db->order_cap + (uint64_t)o_id;"),
 }

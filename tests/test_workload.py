@@ -105,3 +105,22 @@ def test_customer_names():
     # NURand skews the remaining 2,000 per district towards a few names
     counts = np.bincount(last[:, wl.OE_LAST_NAMES:].ravel(), minlength=wl.OE_LAST_NAMES)
     assert counts.max() > 4 * counts.mean()
+
+
+def test_payments_by_last_name_share_and_encoding():
+    """by_name_frac = 0 leaves every payment by id (the same batch as without
+    the option); 0.6 names about 60% of the customers by last name, keyed by
+    the customer's district with a last-name id that exists there."""
+    _, b0, _ = wl.order_entry(seed=9, W=2, n_txns=4000)
+    _, b1, _ = wl.order_entry(seed=9, W=2, n_txns=4000, by_name_frac=0.6)
+    assert not (b0.ops["kind"] == wl.OE_C_PAY_BY_NAME).any()
+    pay = b1.txns["type"] == wl.TXN_PAYMENT
+    third = b1.txns["first_op"][pay].astype(np.int64) + 2
+    by_name = b1.ops["kind"][third] == wl.OE_C_PAY_BY_NAME
+    assert 0.55 < by_name.mean() < 0.65
+    assert (b1.ops["key"][third[by_name]] < 2 * wl.OE_DISTRICTS).all()
+    assert (b1.ops["aux"][third[by_name]] < wl.OE_LAST_NAMES).all()
+    same = np.ones(b1.n_ops, dtype=bool)
+    same[third[by_name]] = False
+    assert np.array_equal(b0.ops[same], b1.ops[same])
+    assert np.array_equal(b0.operands, b1.operands)
