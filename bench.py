@@ -573,16 +573,23 @@ def run_batched(args, rank, world, dist=None):
         entries.append(e)
     torch.cuda.synchronize(dev)
     total_txns = sum(b.n_txns for (_, _, b) in spec)
-    # autotune on the median-size batch
+    # autotune on three size classes (smallest, median, largest batch) over
+    # lanes per txn {1, 2, 4, 8, 16, 32} x warps per block {1, 2, 4, 8, 16, 32}
+    # x two backoff caps; the plan then takes the candidate it runs fastest
     order = sorted(range(len(spec)), key=lambda i: spec[i][2].n_txns)
-    m = order[len(order) // 2]
-    db, tx, n_t, op, od, n_o, rs, rd = entries[m]
-    space = eng.tune_space(lanes=(4, 8, 16, 32), warps=(4, 8, 16), caps=(65536, 1000000, 16000000),
-                           steps=2, warmup=1)
-    best, rep = eng.gcc_autotune(db.handle, "occ", tx.data_ptr(), n_t, op.data_ptr(), od.data_ptr(),
-                                 n_o, rs.data_ptr(), rd.data_ptr(), space)
+    space = eng.tune_space(lanes=(1, 2, 4, 8, 16, 32), warps=(1, 2, 4, 8, 16, 32),
+                           caps=(65536, 1000000), steps=2, warmup=1)
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
+    candidates, tuned = [], []
+    for cls, m in (("small", order[0]), ("median", order[len(order) // 2]), ("large", order[-1])):
+        db, tx, n_t, op, od, n_o, rs, rd = entries[m]
+        best_m, rep = eng.gcc_autotune(db.handle, "occ", tx.data_ptr(), n_t, op.data_ptr(),
+                                       od.data_ptr(), n_o, rs.data_ptr(), rd.data_ptr(), space)
+        candidates.append(best_m)
+        tuned.append({"class": cls, "txns": n_t, "lanes_per_txn": best_m.lanes_per_txn,
+                      "warps_per_block": best_m.warps_per_block,
+                      "backoff_cap_ns": best_m.backoff_cap_ns, "report": rep})
 
     def timed(fn, steps):
         for _ in range(args.warmup):
@@ -600,19 +607,35 @@ def run_batched(args, rank, world, dist=None):
             dist.barrier()
         return e0.elapsed_time(e1) / 1000.0
 
-    def plain():
+    steps = max(1, min(args.steps, 5))
+    best, best_t = candidates[0], None
+    for c in candidates:                              # the plan picks its own point
+        pl = eng.MultiPlan("occ", entries, c)
+        pl.launch(use_graph=True, stream=sh)
+        t = timed(lambda: pl.launch(use_graph=True, stream=sh), 1)
+        pl.close()
+        if best_t is None or t < best_t:
+            best, best_t = c, t
+
+    def plain(scheme="occ", p=None):
         for (db, tx, n_t, op, od, n_o, rs, rd) in entries:
-            db.execute("occ", tx, op, od, n_t, n_o, rs, rd, best, sh)
+            db.execute(scheme, tx, op, od, n_t, n_o, rs, rd, p or best, sh)
 
     plan = eng.MultiPlan("occ", entries, best)
     plan.launch(use_graph=True, stream=sh)            # capture once
+    det_plan = eng.MultiPlan("det", entries)
+    det_plan.launch(use_graph=True, stream=sh)
     torch.cuda.synchronize(dev)
-    steps = max(1, min(args.steps, 5))
     with ClockSampler(dev) as clocks:
         t_plain = timed(plain, steps)
         committed_plain = sum(d.last_stats()["committed"] for d in dbs)
         t_multi = timed(lambda: plan.launch(use_graph=True, stream=sh), steps)
         committed_multi = sum(plan.stats(i)["committed"] for i in range(len(entries)))
+        t_det_plain = timed(lambda: plain("det", eng.params()), steps)
+        committed_det_plain = sum(d.last_stats()["committed"] for d in dbs)
+        t_det = timed(lambda: det_plan.launch(use_graph=True, stream=sh), steps)
+        committed_det = sum(det_plan.stats(i)["committed"] for i in range(len(entries)))
+    det_plan.close()
     plan.close()
     for d in dbs:
         d.close()
@@ -631,7 +654,12 @@ def run_batched(args, rank, world, dist=None):
                                "ms_per_step": 1000 * t_plain / steps},
             "speedup_vs_plain": v_multi / v_plain,
             "autotuned": {"lanes_per_txn": best.lanes_per_txn, "warps_per_block": best.warps_per_block,
-                          "backoff_cap_ns": best.backoff_cap_ns, "report": rep},
+                          "backoff_cap_ns": best.backoff_cap_ns, "size_classes": tuned},
+            "det": {"batched_txn_per_s": committed_det * steps / t_det,
+                    "plain_txn_per_s": committed_det_plain * steps / t_det_plain,
+                    "speedup_vs_plain": (committed_det / t_det) / (committed_det_plain / t_det_plain),
+                    "ms_per_step": 1000 * t_det / steps,
+                    "all_committed": committed_det == total_txns},
             "all_committed": committed_multi == total_txns and committed_plain == total_txns,
             "clocks": clocks.summary()}
 

@@ -410,11 +410,15 @@ typedef struct gcc_multi_batch {
 
 typedef struct gcc_multi_plan gcc_multi_plan;
 
-/* Build a launch plan for `n` batches (at most 256) under OCC, NO_WAIT 2PL or
- * TO: uploads the batch descriptors, allocates the plan's scratch (sort
+/* Build a launch plan for `n` batches (at most 256) under OCC, NO_WAIT 2PL,
+ * TO or DET: uploads the batch descriptors, allocates the plan's scratch (sort
  * buffers for all transactions) and puts every database's control words in a
- * state the scheme can start from.  The batch arrays must stay valid while
- * the plan is used.  Synchronous. */
+ * state the scheme can start from.  Under GCC_DET every batch runs its
+ * database's own prefix-sum evaluation (as gcc_execute's default
+ * deterministic path; n_records * n_fields below 2^32, else
+ * GCC_ERR_CAPACITY), the batches spread over up to eight side streams forked
+ * from and joined into the launch stream, so that their pipelines overlap.
+ * The batch arrays must stay valid while the plan is used.  Synchronous. */
 gcc_status gcc_multi_plan_create(gcc_scheme scheme, const gcc_multi_batch *batches, uint32_t n,
                                  const gcc_exec_params *params, gcc_multi_plan **out);
 

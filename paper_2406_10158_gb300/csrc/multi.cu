@@ -253,6 +253,12 @@ struct gcc_multi_plan {
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     uint32_t launches = 0;
+    // deterministic plans: every database's batch by its own prefix-sum
+    // pipeline (its own scratch), spread over side streams that fork from and
+    // join the launch stream, so that the pipelines overlap
+    std::vector<gcc::ExecArgs> h_args;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> ev;     // [0]: fork, [1 + k]: side stream k done
 };
 
 namespace {
@@ -271,6 +277,10 @@ void free_plan(gcc_multi_plan* pl) {
     cudaFree(pl->sort.v1);
     cudaFree(pl->sort.hist);
     cudaFree(pl->sort.totals);
+    for (cudaStream_t s : pl->side)
+        if (s) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+    for (cudaEvent_t e : pl->ev)
+        if (e) cudaEventDestroy(e);
     if (pl->stream) cudaStreamDestroy(pl->stream);
     delete pl;
 }
@@ -279,9 +289,38 @@ MetaState state_after(gcc_scheme s) {
     return s == GCC_OCC ? META_OCC : s == GCC_TO ? META_TO : META_ZERO;
 }
 
+// Deterministic plans: database i's batch on side stream i mod k, the side
+// streams forked from `st` and joined back into it.
+gcc_status enqueue_det(gcc_multi_plan* pl, cudaStream_t st) {
+    using namespace gcc;
+    const uint32_t k = (uint32_t)pl->side.size();
+    cudaError_t e = cudaEventRecord(pl->ev[0], st);
+    for (uint32_t j = 0; e == cudaSuccess && j < k; ++j) e = cudaStreamWaitEvent(pl->side[j], pl->ev[0], 0);
+    uint32_t launches = 0;
+    for (uint32_t i = 0; e == cudaSuccess && i < pl->n; ++i) {
+        gcc_db* db = pl->dbs[i];
+        cudaStream_t s = pl->side[i % k];
+        e = launch_batch_begin(db->st, db->dbs, GCC_DET, s);
+        if (e == cudaSuccess)
+            e = det_fold_kv(pl->h_args[i], pl->field_bytes, db->sort, db->scan_tmp, db->fold_flags,
+                            db->fold_seg, s);
+        int bits = 0;
+        for (uint64_t v = (uint64_t)db->d.n_fields * db->d.n_records; v; v >>= 1) ++bits;
+        launches += 1 + 2 + 3 * ((bits + 7) / 8) + 4 + 1 + 3 + 2;
+    }
+    for (uint32_t j = 0; e == cudaSuccess && j < k; ++j) {
+        e = cudaEventRecord(pl->ev[1 + j], pl->side[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, pl->ev[1 + j], 0);
+    }
+    if (e != cudaSuccess) return fail(GCC_ERR_CUDA, "multi launch: %s", cudaGetErrorString(e));
+    pl->launches = launches;
+    return GCC_OK;
+}
+
 // The launch sequence, all stream-ordered and allocation-free.
 gcc_status enqueue(gcc_multi_plan* pl, cudaStream_t st) {
     using namespace gcc;
+    if (pl->scheme == GCC_DET) return enqueue_det(pl, st);
     multi_begin<<<1, 256, 0, st>>>(pl->d_args, pl->d_own, pl->n, pl->d_ms, (int)pl->scheme);
     if (pl->n)
         multi_rq_reset<<<dim3(RETRY_QUEUES / 256, pl->n), 256, 0, st>>>(pl->d_args, pl->n);
@@ -343,8 +382,8 @@ gcc_status gcc_multi_plan_create(gcc_scheme scheme, const gcc_multi_batch* b, ui
     if (!b || !out || n == 0) return fail(GCC_ERR_INVALID, "null argument or no batches");
     *out = nullptr;
     if (n > gcc::MAX_BATCHES) return fail(GCC_ERR_CAPACITY, "at most 256 batches per plan");
-    if (scheme != GCC_OCC && scheme != GCC_NO_WAIT_2PL && scheme != GCC_TO)
-        return fail(GCC_ERR_INVALID, "the batched form runs OCC, NO_WAIT 2PL or TO");
+    if (scheme != GCC_OCC && scheme != GCC_NO_WAIT_2PL && scheme != GCC_TO && scheme != GCC_DET)
+        return fail(GCC_ERR_INVALID, "the batched form runs OCC, NO_WAIT 2PL, TO or DET");
     gcc_exec_params p = merged(params);
     gcc_status s = validate_params(p);
     if (s) return s;
@@ -362,6 +401,9 @@ gcc_status gcc_multi_plan_create(gcc_scheme scheme, const gcc_multi_batch* b, ui
             if (b[j].db == db) return fail(GCC_ERR_INVALID, "batch %u: database used twice", i);
         if (b[i].n_txns > db->d.max_batch_txns || b[i].n_ops > db->d.max_batch_ops)
             return fail(GCC_ERR_CAPACITY, "batch %u exceeds its database's maxima", i);
+        if (scheme == GCC_DET && (uint64_t)db->d.n_fields * db->d.n_records >= (1ull << 32))
+            return fail(GCC_ERR_CAPACITY,
+                        "batch %u: deterministic batches need n_records * n_fields below 2^32", i);
         if ((b[i].n_txns && (!b[i].d_txns || !b[i].d_results)) ||
             (b[i].n_ops && (!b[i].d_ops || !b[i].d_operands || !b[i].d_reads)))
             return fail(GCC_ERR_INVALID, "batch %u: null pointer", i);
@@ -442,9 +484,30 @@ gcc_status gcc_multi_plan_create(gcc_scheme scheme, const gcc_multi_batch* b, ui
         a.queue_turn_ns = p.queue_turn_ns;
         a.queue_width = p.queue_width;
         a.queue_after = queue_after_for(p, scheme);
+        if (scheme == GCC_DET) {
+            // the database's own scratch and staging limit, as a plain launch
+            a.max_ops = db->d.max_ops_per_txn;
+            a.need = db->need;
+            a.order_key_uses_base = 0;
+            continue;                    // control words are not used
+        }
         // control words in a state this scheme can start from
         if ((s = prepare_meta(db, scheme, pl->stream))) return bail(s);
         db->meta_state = state_after(scheme);
+    }
+    if (scheme == GCC_DET) {
+        pl->h_args = args;
+        const uint32_t k = std::min<uint32_t>(n, 8);
+        pl->side.assign(k, nullptr);
+        pl->ev.assign(k + 1, nullptr);
+        for (auto& st2 : pl->side)
+            if (cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking) != cudaSuccess)
+                return bail(fail(GCC_ERR_CUDA, "cannot create stream"));
+        for (auto& e : pl->ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+                return bail(fail(GCC_ERR_CUDA, "cannot create event"));
+        *out = pl;
+        return GCC_OK;
     }
     gcc::MultiState ms{};
     ms.total = total;
@@ -480,7 +543,8 @@ gcc_status gcc_multi_launch(gcc_multi_plan* pl, int use_graph, void* stream) {
     if (!pl) return fail(GCC_ERR_INVALID, "null plan");
     if (cudaSetDevice(pl->device) != cudaSuccess) return fail(GCC_ERR_CUDA, "cannot select device");
     for (gcc_db* db : pl->dbs)
-        if (db->meta_state != META_ZERO && db->meta_state != state_after(pl->scheme))
+        if (pl->scheme != GCC_DET && db->meta_state != META_ZERO &&
+            db->meta_state != state_after(pl->scheme))
             return fail(GCC_ERR_INVALID, "a database ran another scheme since the plan was made");
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : pl->stream;
     if (!use_graph) return enqueue(pl, st);

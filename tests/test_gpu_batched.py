@@ -46,7 +46,7 @@ def make_set(eng, n_db=6, seed=3, spec=None):
     return entries, dbs
 
 
-def check_all(eng, plan, dbs, states):
+def check_all(eng, plan, dbs, states, det=False):
     import torch
     torch.cuda.synchronize()
     new_states = []
@@ -58,20 +58,22 @@ def check_all(eng, plan, dbs, states):
         assert st["committed"] == batch.n_txns, (i, st)
         rep = oracle.replay_check(state, final, batch, r, rd)
         assert rep["ok"], (i, rep)
+        if det:                           # the deterministic outcome: id order
+            assert np.array_equal(r["commit_order"], np.arange(batch.n_txns)), i
         new_states.append(final)
     return new_states
 
 
-@pytest.mark.parametrize("scheme", ["occ", "2pl", "to"])
+@pytest.mark.parametrize("scheme", ["occ", "2pl", "to", "det"])
 def test_batched_form_replays(eng, scheme):
     entries, dbs = make_set(eng)
     plan = eng.MultiPlan(scheme, entries, eng.params(backoff_cap_ns=16_000_000))
     states = [t for (_, t, _, _, _) in dbs]
     plan.launch(use_graph=False)
-    states = check_all(eng, plan, dbs, states)
+    states = check_all(eng, plan, dbs, states, det=scheme == "det")
     for _ in range(2):                    # graph capture, then a replay
         plan.launch(use_graph=True)
-        states = check_all(eng, plan, dbs, states)
+        states = check_all(eng, plan, dbs, states, det=scheme == "det")
     plan.close()
     for (db, *_rest) in dbs:
         db.close()
@@ -86,10 +88,10 @@ def test_batched_form_full_size(eng):
     spec = wl.batched_kv(wl.SEEDS[3], n_db=64)
     entries, dbs = make_set(eng, spec=spec)
     states = [t for (_, t, _, _, _) in dbs]
-    for scheme in ("occ", "2pl", "to"):
+    for scheme in ("occ", "2pl", "to", "det"):
         plan = eng.MultiPlan(scheme, entries, eng.params(backoff_cap_ns=16_000_000))
         plan.launch(use_graph=True)
-        states = check_all(eng, plan, dbs, states)
+        states = check_all(eng, plan, dbs, states, det=scheme == "det")
         plan.close()
     for (db, *_rest) in dbs:
         db.close()
