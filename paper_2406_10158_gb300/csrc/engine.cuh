@@ -191,14 +191,16 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// One ticket from a counter per calling lane, with one atomic per warp:
-// the lanes active at the call share a single atomicAdd.  *n_atom (when
-// given) counts the atomic on the lane that issues it.
+// One ticket from a counter per calling lane, with one atomic per warp and
+// counter: the lanes active at the call that name the same counter share a
+// single atomicAdd (lanes of one warp may name different counters -- in the
+// batched form, groups of one warp work on different databases).  *n_atom
+// (when given) counts the atomic on the lane that issues it.
 __device__ __forceinline__ unsigned long long agg_ticket(unsigned long long* ctr,
                                                         unsigned step = 1,
                                                         uint32_t* n_atom = nullptr) {
-    unsigned mask = __activemask();
-    int leader = __ffs(mask) - 1;
+    const unsigned mask = __match_any_sync(__activemask(), reinterpret_cast<uintptr_t>(ctr));
+    const int leader = __ffs(mask) - 1;
     unsigned long long base = 0;
     if ((threadIdx.x & 31) == leader) {
         base = atomicAdd(ctr, (unsigned long long)__popc(mask) * step);
@@ -213,8 +215,8 @@ __device__ __forceinline__ unsigned long long agg_ticket(unsigned long long* ctr
 // carries the release) also sees everything that preceded this ticket.
 __device__ __forceinline__ unsigned long long agg_ticket_acq_rel(unsigned long long* ctr,
                                                                 uint32_t* n_atom = nullptr) {
-    unsigned mask = __activemask();
-    int leader = __ffs(mask) - 1;
+    const unsigned mask = __match_any_sync(__activemask(), reinterpret_cast<uintptr_t>(ctr));
+    const int leader = __ffs(mask) - 1;
     unsigned long long base = 0;
     if ((threadIdx.x & 31) == leader) {
         const unsigned long long inc = (unsigned long long)__popc(mask);
