@@ -344,6 +344,36 @@ def test_det_wait_budget_returns(eng):
         check(table, db.read_kv(), batch, res, reads, "det", stats)
 
 
+def test_det_gap_in_op_ranges_runs_out_its_waits(eng):
+    """A deterministic batch whose transaction op ranges leave an op out: run
+    op by op, a later access to that op's record waits for it, the wait runs
+    out of its (short) budget, and the transaction ends TIMEOUT with the
+    wait-budget flag while the others commit; the prefix-sum path leaves the
+    uncovered op out of its access table and commits everything.  The
+    database is usable afterwards."""
+    nrec = 16
+    table = wl.kv_table_splitmix(5, nrec, 1)
+    full = wl.kv_batch_from_lists([
+        [(1, 0, 1, 5, 0), (2, 0, 0, 0, 0)],
+        [(7, 0, 1, 9, 0)],                              # becomes the uncovered op
+        [(7, 0, 1, 3, 0), (3, 0, 0, 0, 0)],
+    ])
+    txns = full.txns[[0, 2]].copy()                     # op 2 belongs to no transaction
+    gap = wl.KVBatch(txns=txns, ops=full.ops, operands=full.operands)
+    with eng.Database("kv", n_records=nrec, n_fields=1, field_bytes=8, max_ops_per_txn=4,
+                      max_batch_txns=8) as db:
+        db.load_kv(table)
+        res, reads, stats = db.run("det", gap, eng.params(det_dataflow=1,
+                                                         wait_budget_ns=20_000_000))
+        assert res["status"].tolist() == [oracle.ST_COMMITTED, oracle.ST_TIMEOUT], res
+        assert "wait_budget" in stats["errors"]
+        db.load_kv(table)
+        res, reads, stats = db.run("det", gap)
+        assert (res["status"] == oracle.ST_COMMITTED).all()
+        ref = oracle.serial(table, wl.KVBatch(txns=txns, ops=full.ops, operands=full.operands))
+        assert np.array_equal(db.read_kv(), ref[0])
+
+
 def test_schemes_share_one_database(eng):
     """Schemes alternate on one database; each batch starts from the previous
     batch's final state and replays exactly."""

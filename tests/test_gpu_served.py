@@ -152,6 +152,41 @@ def test_served_same_alone_and_in_the_mix(eng, scheme):
     assert np.array_equal(ref_final, f0) and np.array_equal(ref_reads, r0)
 
 
+def test_server_drains_after_the_producer_stops(eng):
+    """A producer enqueues requests in bursts, pumping between them, and then
+    stops mid-stream: drain completes every admitted request, and their
+    history replays exactly."""
+    nrec = 1 << 12
+    table = wl.kv_table_splitmix(51, nrec, 4)
+    kv = wl.kv_batch(52, nrec=nrec, nfields=4, n_txns=3000, read_ratio=0.5, theta=0.9)
+    with eng.Database("kv", n_records=nrec, n_fields=4, field_bytes=8, max_batch_txns=256) as db:
+        db.load_kv(table)
+        srv = eng.Server([(db, "occ", 256, 0, 50_000, 3)], eng.params(backoff_cap_ns=16_000_000))
+        try:
+            sent = 0
+            for burst in range(7):                      # then the producer stops
+                for t in range(sent, sent + 300):
+                    f, nops = int(kv.txns["first_op"][t]), int(kv.txns["n_ops"][t])
+                    srv.enqueue(0, kv.txns[t:t + 1], kv.ops[f:f + nops],
+                                kv.operands[f:f + nops].astype(np.uint64), srv.now_ns())
+                sent += 300
+                srv.pump()
+            srv.drain()
+            comp, reads = srv.completions()
+        finally:
+            srv.close()
+        final = db.read_kv()
+    assert comp.size == sent and (comp["status"] == oracle.ST_COMMITTED).all()
+    sub = wl.select(kv, comp["request"].astype(np.int64))
+    res = np.zeros(comp.size, dtype=wl.RESULT_DTYPE)
+    res["status"] = oracle.ST_COMMITTED
+    order = np.lexsort((comp["commit_order"], comp["batch_seq"]))
+    res["commit_order"][order] = np.arange(comp.size)
+    assert np.array_equal(np.sort(comp["request"]), np.arange(sent))
+    rep = oracle.replay_check(table, final, sub, res, reads[:sub.n_ops])
+    assert rep["ok"], rep
+
+
 def test_server_rejects_requests_larger_than_a_batch(eng):
     """A database whose batches hold fewer ops than a transaction may have:
     a request that no batch of its lane can hold is refused on the host
