@@ -67,7 +67,9 @@ def parse_args(argv=None):
     p.add_argument("--n-db", type=int, default=64, help="batched form: databases")
     p.add_argument("--rates", default="1e5,1e6,1e7,1e8",
                    help="served form: offered rates (txn/s), comma-separated")
-    p.add_argument("--requests", type=int, default=1 << 18, help="served form: requests per rate")
+    p.add_argument("--requests", type=int, default=10_000_000,
+                   help="served form: most requests per rate (each rate runs at most 10 s "
+                        "of arrivals)")
     p.add_argument("--kv-scheme", default="det", choices=SCHEMES, help="served form: key-value lane")
     p.add_argument("--oe-scheme", default="det", choices=SCHEMES, help="served form: order-entry lane")
     return p.parse_args(argv)
@@ -673,7 +675,9 @@ def run_served(args, rank, world):
     under its own scheme (--kv-scheme, --oe-scheme; deterministic by default),
     at each offered rate: committed txns/s and p50/p99 latency (arrival to
     result on the host), against plain per-batch launches of the same requests
-    (submit, wait, next)."""
+    (submit, wait, next).  Each rate runs min(--requests, 10 s of arrivals)
+    requests -- 10 s or 10^7 requests at the default -- taken as a prefix of
+    one trace generated once."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -681,20 +685,23 @@ def run_served(args, rank, world):
     from paper_2406_10158_gb300 import workload as wl
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    n = args.requests
+    rates = [float(r) for r in args.rates.split(",")]
+    per_rate = {r: int(min(args.requests, max(1.0, 10.0 * r))) for r in rates}
+    n = max(per_rate.values())
     nrec = 1 << 24
-    table = wl.kv_table_splitmix(wl.SEEDS[4], nrec, 8)
-    kv = wl.kv_batch(wl.derive_seed(wl.SEEDS[4], 1), nrec=nrec, nfields=8, n_txns=n,
-                     read_ratio=0.8, theta=0.8)
-    oe0, oe, cap = wl.order_entry(seed=wl.SEEDS[4], W=8, n_txns=n)   # every rate reloads it
+    t_gen = time.time()
     rng = np.random.default_rng(7)
     lane_of = (rng.random(n) < 0.5).astype(np.uint32)
+    n_kv, n_oe = int(np.count_nonzero(lane_of == 0)), int(np.count_nonzero(lane_of == 1))
+    table = wl.kv_table_splitmix(wl.SEEDS[4], nrec, 8)
+    kv = wl.kv_batch(wl.derive_seed(wl.SEEDS[4], 1), nrec=nrec, nfields=8, n_txns=max(1, n_kv),
+                     read_ratio=0.8, theta=0.8)
+    oe0, oe, cap = wl.order_entry(seed=wl.SEEDS[4], W=8, n_txns=max(1, n_oe))  # every rate reloads it
     trace = wl.interleave([kv, oe], lane_of)
+    gen_s = time.time() - t_gen
     max_batch = 1 << 14
-    lanes_kv = (args.kv_scheme, max_batch)
     oe_scheme = args.oe_scheme
     results = []
-    rates = [float(r) for r in args.rates.split(",")]
 
     def fresh():
         dkv = eng.Database("kv", n_records=nrec, n_fields=8, field_bytes=8,
@@ -707,11 +714,13 @@ def run_served(args, rank, world):
 
     with ClockSampler(dev) as clocks:
         for rate in rates:
-            arrivals = wl.poisson_arrivals(wl.SEEDS[4] + int(rate), n, rate)
+            m = per_rate[rate]
+            sub = trace if m == n else wl.select(trace, np.arange(m))
+            arrivals = wl.poisson_arrivals(wl.SEEDS[4] + int(rate), m, rate)
             dkv, doe = fresh()
-            srv = eng.Server([(dkv, lanes_kv[0], max_batch, 0, 100_000, 4),
+            srv = eng.Server([(dkv, args.kv_scheme, max_batch, 0, 100_000, 4),
                               (doe, oe_scheme, max_batch, 0, 100_000, 4)])
-            comp, _ = srv.run_trace(lane_of, trace, arrivals)
+            comp, _ = srv.run_trace(lane_of[:m], sub, arrivals)
             tots = [srv.lane_totals(0), srv.lane_totals(1)]
             srv.close()
             dkv.close()
@@ -719,19 +728,24 @@ def run_served(args, rank, world):
             ok = comp["status"] == 1
             lat = (comp["done_ns"] - comp["arrival_ns"]).astype(np.float64) / 1e3
             span = (comp["done_ns"].max() - comp["arrival_ns"].min()) / 1e9
-            results.append({"offered_txn_per_s": rate, "committed_txn_per_s": float(ok.sum() / span),
+            results.append({"offered_txn_per_s": rate, "requests": m,
+                            "arrival_span_s": round(float(arrivals[-1]) / 1e9, 3),
+                            "committed_txn_per_s": float(ok.sum() / span),
                             "p50_latency_us": float(np.percentile(lat, 50)),
                             "p99_latency_us": float(np.percentile(lat, 99)),
                             "abort_rate": sum(t["aborts"] for t in tots) / max(1, sum(t["committed"] for t in tots)),
                             "batches": sum(t["batches"] for t in tots),
                             "all_committed": bool(ok.all())})
+            del comp, sub
         # plain per-batch launches of the same requests: submit, wait, next
         dkv, doe = fresh()
-        subs = [wl.select(trace, np.nonzero(lane_of == l)[0]) for l in (0, 1)]
+        m = per_rate[max(rates)]
+        lanes = lane_of[:m]
+        subs = [wl.select(trace, np.nonzero(lanes == l)[0]) for l in (0, 1)]
         t0 = time.perf_counter()
         committed = 0
         for start in range(0, max(s.n_txns for s in subs), max_batch):
-            for l, (db, scheme) in enumerate(((dkv, lanes_kv[0]), (doe, oe_scheme))):
+            for l, (db, scheme) in enumerate(((dkv, args.kv_scheme), (doe, oe_scheme))):
                 idx = np.arange(start, min(start + max_batch, subs[l].n_txns))
                 if idx.size:
                     _, _, st = db.run(scheme, wl.select(subs[l], idx))
@@ -744,12 +758,14 @@ def run_served(args, rank, world):
             "unit": "txn/s", "n_gpus": 1, "steps": len(rates), "warmup": 0,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"{n} requests, 50/50 kv (2^24 x 8 u64, 16 ops, zipf 0.8, 80% "
-                                   f"reads, {lanes_kv[0]}) and order-entry (W=8, {oe_scheme}), "
-                                   f"poisson arrivals",
-                       "max_batch_txns": max_batch, "max_delay_us": 100, "depth": 4},
+            "config": {"workload": f"50/50 kv (2^24 x 8 u64, 16 ops, zipf 0.8, 80% reads, "
+                                   f"{args.kv_scheme}) and order-entry (W=8, {oe_scheme}), "
+                                   f"poisson arrivals, min({args.requests}, 10 s of arrivals) "
+                                   f"requests per rate",
+                       "max_batch_txns": max_batch, "max_delay_us": 100, "depth": 4,
+                       "trace_generation_s": round(gen_s, 1)},
             "p99_latency_us": best["p99_latency_us"], "rates": results,
-            "plain_per_batch": {"value": committed / plain_s, "unit": "txn/s"},
+            "plain_per_batch": {"value": committed / plain_s, "unit": "txn/s", "requests": m},
             "speedup_vs_plain": best["committed_txn_per_s"] / (committed / plain_s),
             "clocks": clocks.summary()}
 
