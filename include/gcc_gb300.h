@@ -5,7 +5,7 @@
  * under one of six concurrency-control schemes and returns, per transaction,
  * its commit status, its position in a commit order and the values it read.
  * It follows the paper's statement of the problem: transactions are run in
- * batches, one worker per transaction (Sec. III-B); read and write sets are
+ * batches, one worker per transaction (Sec. III-C); read and write sets are
  * known before execution (Sec. IV-A, "Constraints"); an aborted transaction
  * restarts until it commits (Sec. IV-A, "Experimental Procedure"); every scheme
  * is serializable (Sec. III-E).  The committed transactions, executed serially
@@ -301,7 +301,7 @@ uint64_t gcc_table_bytes(const gcc_db *db, uint32_t table_id);
  * (src_on_device = 0) or device pointer, and reset the concurrency-control
  * words.  Synchronous.  Paper: the host generates the tables and transfers
  * them to GPU memory before execution (Sec. IV-A, "Experimental Procedure";
- * the CPU side coordinates data generation and initialisation, Sec. III-B).
+ * the CPU side coordinates data generation and initialisation, Sec. III-C).
  * Errors: GCC_ERR_INVALID (NULL db or src, bad table id, nbytes differs from
  * the table's size), GCC_ERR_CUDA.  src stays owned by the caller.  Key-value layout: field-major, slot (key, field) at
  * byte (field * n_records + key) * field_bytes. */
@@ -333,7 +333,7 @@ gcc_status gcc_db_read_table(gcc_db *db, uint32_t table_id, void *dst,
 gcc_status gcc_default_params(gcc_exec_params *p);
 
 /* Submit a batch asynchronously.  Paper: transactions run in batches with
- * one worker per transaction (Sec. III-B, batch execution model); every
+ * one worker per transaction (Sec. III-C, batch execution model); every
  * transaction's reads and writes are known before execution, given here as
  * its op list (Sec. IV-A, "Constraints"); a transaction that fails on a
  * conflict restarts until it commits (Sec. IV-A, "Experimental Procedure");
@@ -410,8 +410,8 @@ typedef struct gcc_multi_batch {
 
 typedef struct gcc_multi_plan gcc_multi_plan;
 
-/* Build a launch plan for `n` batches (at most 256) under OCC, NO_WAIT 2PL,
- * TO or DET: uploads the batch descriptors, allocates the plan's scratch (sort
+/* Build a launch plan for `n` batches (at most 256) under any scheme:
+ * uploads the batch descriptors, allocates the plan's scratch (sort
  * buffers for all transactions) and puts every database's control words in a
  * state the scheme can start from.  Under GCC_DET every batch runs its
  * database's own prefix-sum evaluation (as gcc_execute's default
@@ -424,7 +424,11 @@ gcc_status gcc_multi_plan_create(gcc_scheme scheme, const gcc_multi_batch *batch
 
 /* Enqueue one execution of every batch of the plan on `stream` (NULL = the
  * plan's stream): batch states reset, one persistent kernel over all
- * transactions, commit ranks.  With use_graph != 0 the sequence is captured
+ * transactions (OCC, TO and the two 2PL schemes, TicToc, MVCC; MVCC then
+ * writes every database's newest versions into its table), commit ranks
+ * (OCC and TO by the plan's shared clock, TicToc by (timestamp, sequence
+ * number), MVCC by each batch's own timestamps, both 2PL schemes by each
+ * database's lock-point counter).  With use_graph != 0 the sequence is captured
  * once into a CUDA graph (on the plan's stream) and replayed.  Allocates
  * nothing.  Between launches, run no other scheme on the plan's databases
  * (GCC_ERR_INVALID otherwise). */

@@ -136,7 +136,8 @@ __global__ void multi_begin(const ExecArgs* __restrict__ args, DbState* const* _
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
         BatchState z{};
-        z.ticket_base = scheme == GCC_TO ? to : occ;
+        // MVCC's timestamps count from 1 in every batch (its own counter)
+        z.ticket_base = scheme == GCC_TO ? to : scheme == GCC_MVCC ? 0ull : occ;
         *args[i].st = z;
     }
 }
@@ -211,19 +212,42 @@ cudaError_t multi_launch_kernel(const ExecArgs* args, const uint32_t* prefix, ui
 }
 
 int occupancy_for(gcc_scheme scheme, uint32_t fb, int block, size_t smem) {
+#define GCC_MULTI_OCC(SC)                                                        \
+    case SC:                                                                     \
+        return fb == 16 ? multi_occupancy<SC, 16>(block, smem)                   \
+                        : multi_occupancy<SC, 8>(block, smem);
     switch (scheme) {
-        case GCC_NO_WAIT_2PL:
-            return fb == 16 ? multi_occupancy<GCC_NO_WAIT_2PL, 16>(block, smem)
-                            : multi_occupancy<GCC_NO_WAIT_2PL, 8>(block, smem);
-        case GCC_TO:
-            return fb == 16 ? multi_occupancy<GCC_TO, 16>(block, smem)
-                            : multi_occupancy<GCC_TO, 8>(block, smem);
-        case GCC_OCC:
-            return fb == 16 ? multi_occupancy<GCC_OCC, 16>(block, smem)
-                            : multi_occupancy<GCC_OCC, 8>(block, smem);
+        GCC_MULTI_OCC(GCC_NO_WAIT_2PL)
+        GCC_MULTI_OCC(GCC_TO)
+        GCC_MULTI_OCC(GCC_OCC)
+        GCC_MULTI_OCC(GCC_TICTOC)
+        GCC_MULTI_OCC(GCC_2PL_WAIT_DIE)
+        GCC_MULTI_OCC(GCC_MVCC)
         default:
             return 0;
     }
+#undef GCC_MULTI_OCC
+}
+
+// TicToc's serial order over every batch of the plan: three stable passes
+// (sequence number, then the timestamp's low and high words; pass 0 keys by
+// position, later passes re-key the previous pass's order in place), as in
+// the single-batch path; the batch grouping follows.
+__global__ void multi_tt_keys(const ExecArgs* __restrict__ args, const uint32_t* __restrict__ prefix,
+                              uint32_t n, uint64_t total, int pass, uint32_t* __restrict__ keys,
+                              uint32_t* __restrict__ vals) {
+    const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    const uint32_t g = pass == 0 ? (uint32_t)p : vals[p];
+    const uint32_t i = find_batch(prefix, n, g);
+    const ExecArgs& a = args[i];
+    const uint32_t t = g - prefix[i];
+    uint32_t k = 0xffffffffu;
+    if (a.results[t].status == GCC_TXN_COMMITTED)
+        k = pass == 0 ? a.seq[t] : pass == 1 ? (uint32_t)a.order_key[t]
+                                             : (uint32_t)(a.order_key[t] >> 32);
+    keys[p] = k;
+    vals[p] = g;
 }
 
 inline unsigned blocks_for(uint64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -286,7 +310,8 @@ void free_plan(gcc_multi_plan* pl) {
 }
 
 MetaState state_after(gcc_scheme s) {
-    return s == GCC_OCC ? META_OCC : s == GCC_TO ? META_TO : META_ZERO;
+    return s == GCC_OCC ? META_OCC : s == GCC_TO ? META_TO : s == GCC_TICTOC ? META_TICTOC
+                                                                             : META_ZERO;
 }
 
 // Deterministic plans: database i's batch on side stream i mod k, the side
@@ -329,39 +354,60 @@ gcc_status enqueue(gcc_multi_plan* pl, cudaStream_t st) {
         const uint32_t lanes = pl->p.lanes_per_txn;
         const uint64_t dl = pl->p.deadline_ns;
         switch (pl->scheme) {
-            case GCC_NO_WAIT_2PL:
-                e = pl->field_bytes == 16
-                        ? multi_launch_kernel<GCC_NO_WAIT_2PL, 16>(pl->d_args, pl->d_prefix, pl->n, pl->d_ms, lanes, pl->max_ops, dl, pl->grid, pl->block, pl->smem, st)
-                        : multi_launch_kernel<GCC_NO_WAIT_2PL, 8>(pl->d_args, pl->d_prefix, pl->n, pl->d_ms, lanes, pl->max_ops, dl, pl->grid, pl->block, pl->smem, st);
-                break;
-            case GCC_TO:
-                e = pl->field_bytes == 16
-                        ? multi_launch_kernel<GCC_TO, 16>(pl->d_args, pl->d_prefix, pl->n, pl->d_ms, lanes, pl->max_ops, dl, pl->grid, pl->block, pl->smem, st)
-                        : multi_launch_kernel<GCC_TO, 8>(pl->d_args, pl->d_prefix, pl->n, pl->d_ms, lanes, pl->max_ops, dl, pl->grid, pl->block, pl->smem, st);
-                break;
+#define GCC_MULTI_CASE(SC)                                                                         \
+    case SC:                                                                                       \
+        e = pl->field_bytes == 16                                                                  \
+                ? multi_launch_kernel<SC, 16>(pl->d_args, pl->d_prefix, pl->n, pl->d_ms, lanes,     \
+                                              pl->max_ops, dl, pl->grid, pl->block, pl->smem, st)  \
+                : multi_launch_kernel<SC, 8>(pl->d_args, pl->d_prefix, pl->n, pl->d_ms, lanes,      \
+                                             pl->max_ops, dl, pl->grid, pl->block, pl->smem, st);  \
+        break;
+            GCC_MULTI_CASE(GCC_NO_WAIT_2PL)
+            GCC_MULTI_CASE(GCC_TO)
+            GCC_MULTI_CASE(GCC_OCC)
+            GCC_MULTI_CASE(GCC_TICTOC)
+            GCC_MULTI_CASE(GCC_2PL_WAIT_DIE)
+            GCC_MULTI_CASE(GCC_MVCC)
+#undef GCC_MULTI_CASE
             default:
-                e = pl->field_bytes == 16
-                        ? multi_launch_kernel<GCC_OCC, 16>(pl->d_args, pl->d_prefix, pl->n, pl->d_ms, lanes, pl->max_ops, dl, pl->grid, pl->block, pl->smem, st)
-                        : multi_launch_kernel<GCC_OCC, 8>(pl->d_args, pl->d_prefix, pl->n, pl->d_ms, lanes, pl->max_ops, dl, pl->grid, pl->block, pl->smem, st);
+                e = cudaErrorInvalidValue;
                 break;
         }
     }
     uint32_t launches = 3;
-    if (e == cudaSuccess && pl->scheme != GCC_NO_WAIT_2PL && pl->total) {
-        multi_rank_keys<<<blocks_for(pl->total, 256), 256, 0, st>>>(pl->d_args, pl->d_prefix, pl->n,
-                                                                 pl->total, pl->sort.k0, pl->sort.v0);
+    // MVCC: each database's newest versions into its table before the ranks
+    // (the version store lives in the database's own scratch)
+    for (uint32_t i = 0; e == cudaSuccess && pl->scheme == GCC_MVCC && i < pl->n; ++i) {
+        e = launch_mv_flatten(pl->h_args[i], pl->field_bytes, st);
+        launches += 1;
+    }
+    const bool dense = pl->scheme == GCC_NO_WAIT_2PL || pl->scheme == GCC_2PL_WAIT_DIE;
+    if (e == cudaSuccess && !dense && pl->total) {
         uint32_t *sk, *sv;
-        e = radix_sort_pairs(pl->sort, pl->total, 32, &sk, &sv, st);   // by timestamp
+        if (pl->scheme == GCC_TICTOC) {
+            // (timestamp, sequence number), by three stable passes
+            for (int pass = 0; e == cudaSuccess && pass < 3; ++pass) {
+                multi_tt_keys<<<blocks_for(pl->total, 256), 256, 0, st>>>(
+                    pl->d_args, pl->d_prefix, pl->n, pl->total, pass, pl->sort.k0, pl->sort.v0);
+                e = radix_sort_pairs(pl->sort, pl->total, 32, &sk, &sv, st);
+            }
+            launches += 3 * (1 + 12);
+        } else {
+            multi_rank_keys<<<blocks_for(pl->total, 256), 256, 0, st>>>(pl->d_args, pl->d_prefix, pl->n,
+                                                                     pl->total, pl->sort.k0, pl->sort.v0);
+            e = radix_sort_pairs(pl->sort, pl->total, 32, &sk, &sv, st);   // by timestamp
+            launches += 1 + 12;
+        }
         if (e == cudaSuccess) {
             multi_batch_keys<<<blocks_for(pl->total, 256), 256, 0, st>>>(pl->d_prefix, pl->n, pl->total,
                                                                       sk, sv);
-            // the second sort reads from (k0, v0): four timestamp passes end there
+            // the second sort reads from (k0, v0): four-pass sorts end there
             e = radix_sort_pairs(pl->sort, pl->total, 8, &sk, &sv, st);  // stably by batch
         }
         if (e == cudaSuccess)
             multi_ranks<<<blocks_for(pl->total, 256), 256, 0, st>>>(pl->d_args, pl->d_prefix, pl->n,
                                                                  pl->total, sv);
-        launches += 1 + 12 + 1 + 3 + 1;
+        launches += 1 + 3 + 1;
     }
     if (e == cudaSuccess) {
         multi_end<<<1, 256, 0, st>>>(pl->d_own, pl->n, pl->d_ms);
@@ -382,8 +428,7 @@ gcc_status gcc_multi_plan_create(gcc_scheme scheme, const gcc_multi_batch* b, ui
     if (!b || !out || n == 0) return fail(GCC_ERR_INVALID, "null argument or no batches");
     *out = nullptr;
     if (n > gcc::MAX_BATCHES) return fail(GCC_ERR_CAPACITY, "at most 256 batches per plan");
-    if (scheme != GCC_OCC && scheme != GCC_NO_WAIT_2PL && scheme != GCC_TO && scheme != GCC_DET)
-        return fail(GCC_ERR_INVALID, "the batched form runs OCC, NO_WAIT 2PL, TO or DET");
+    if ((unsigned)scheme > GCC_MVCC) return fail(GCC_ERR_INVALID, "unknown scheme %d", (int)scheme);
     gcc_exec_params p = merged(params);
     gcc_status s = validate_params(p);
     if (s) return s;
@@ -484,6 +529,13 @@ gcc_status gcc_multi_plan_create(gcc_scheme scheme, const gcc_multi_batch* b, ui
         a.queue_turn_ns = p.queue_turn_ns;
         a.queue_width = p.queue_width;
         a.queue_after = queue_after_for(p, scheme);
+        a.seq = db->fold_flags;                  // TicToc: sequence numbers
+        a.mv_wts = db->sort.k0;                  // MVCC: the database's version store
+        a.mv_next = db->sort.v0;
+        a.mv_field = db->sort.k1;
+        a.mv_rec = db->sort.v1;
+        a.mv_val = static_cast<ulonglong2*>(db->fold_seg);
+        a.mv_slot = db->mv_slot;
         if (scheme == GCC_DET) {
             // the database's own scratch and staging limit, as a plain launch
             a.max_ops = db->d.max_ops_per_txn;
@@ -495,8 +547,8 @@ gcc_status gcc_multi_plan_create(gcc_scheme scheme, const gcc_multi_batch* b, ui
         if ((s = prepare_meta(db, scheme, pl->stream))) return bail(s);
         db->meta_state = state_after(scheme);
     }
+    pl->h_args = args;
     if (scheme == GCC_DET) {
-        pl->h_args = args;
         const uint32_t k = std::min<uint32_t>(n, 8);
         pl->side.assign(k, nullptr);
         pl->ev.assign(k + 1, nullptr);

@@ -109,8 +109,8 @@ def test_multi_plan_checks(lib):
     expect(lib, lib.gcc_multi_plan_create(2, many, 257, None, ctypes.byref(out)), CAPACITY,
            ["256"])
     one = (eng.MultiBatch * 1)()
-    expect(lib, lib.gcc_multi_plan_create(3, one, 1, None, ctypes.byref(out)), INVALID,
-           ["batched form"])
+    expect(lib, lib.gcc_multi_plan_create(7, one, 1, None, ctypes.byref(out)), INVALID,
+           ["unknown scheme"])
     bad = eng.ExecParams(lanes_per_txn=3)
     expect(lib, lib.gcc_multi_plan_create(2, one, 1, ctypes.byref(bad), ctypes.byref(out)),
            INVALID, ["lanes_per_txn"])

@@ -64,7 +64,7 @@ def check_all(eng, plan, dbs, states, det=False):
     return new_states
 
 
-@pytest.mark.parametrize("scheme", ["occ", "2pl", "to", "det"])
+@pytest.mark.parametrize("scheme", ["occ", "2pl", "2pl_wd", "to", "tictoc", "mvcc", "det"])
 def test_batched_form_replays(eng, scheme):
     entries, dbs = make_set(eng)
     plan = eng.MultiPlan(scheme, entries, eng.params(backoff_cap_ns=16_000_000))
@@ -83,12 +83,12 @@ def test_batched_form_replays(eng, scheme):
 def test_batched_form_full_size(eng):
     """The batched workload as the benchmark builds it: 64 databases of
     2^16..2^22 records (log-uniform) x 8 u64 fields, batches of 1,000 ..
-    262,144 txns of 4..64 ops at Zipf 0.8, in one graph-replayed persistent
-    launch per scheme; every database's history replays exactly."""
+    262,144 txns of 4..64 ops at Zipf 0.8, in one graph-replayed plan per
+    scheme (every scheme); every database's history replays exactly."""
     spec = wl.batched_kv(wl.SEEDS[3], n_db=64)
     entries, dbs = make_set(eng, spec=spec)
     states = [t for (_, t, _, _, _) in dbs]
-    for scheme in ("occ", "2pl", "to", "det"):
+    for scheme in ("occ", "2pl", "2pl_wd", "to", "tictoc", "mvcc", "det"):
         plan = eng.MultiPlan(scheme, entries, eng.params(backoff_cap_ns=16_000_000))
         plan.launch(use_graph=True)
         states = check_all(eng, plan, dbs, states, det=scheme == "det")
