@@ -503,9 +503,16 @@ def run_ours(args, rank, world, dist):
         # second bound: one uncontended link of the engine's own commit
         # sequence per committed writer of the hottest record
         "link_ns": round(probe["occ_link_ns"], 1),
+        "link_max_ns": round(probe["occ_link_max_ns"], 1),
         "link_kind": "measured gcc_probe_memory occ_link_ns (acquire, CAS, acq_rel timestamp, "
-                     "validation load, store, release publish; one thread)",
-        "link_bound_ms": round(link_ms, 3), "link_frac": round(link_ms / kernel_ms, 4)}
+                     "validation load, store, release publish; one thread, least over eight "
+                     "SM placements; link_max_ns the greatest)",
+        "link_bound_ms": round(link_ms, 3), "link_frac": round(link_ms / kernel_ms, 4),
+        # third bound: a bare hand-off per link, two dependent L2 atomics (the
+        # lock and the publish) and nothing else
+        "handoff_ns": round(2 * probe["l2_atomic_ns"], 1),
+        "handoff_bound_ms": round(hot["max_writes"] * 2 * probe["l2_atomic_ns"] / 1e6, 3),
+        "handoff_frac": round(hot["max_writes"] * 2 * probe["l2_atomic_ns"] / 1e6 / kernel_ms, 4)}
     # L2 atomic throughput the execute kernel achieved, against distinct-word CAS
     atom_gops = stats["atomics"] / (kernel_ms / 1000.0) / 1e9
     roofline["atomics"] = {

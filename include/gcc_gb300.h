@@ -617,14 +617,19 @@ typedef struct gcc_memory_probe {
     uint32_t lock_best_contenders;  /* contending warps at lock_handoff_ns */
     uint32_t occ_best_contenders;   /* contending warps at occ_cycle_ns */
     double fence_ns;           /* fence.acq_rel.gpu with no memory operation in
-                                  flight, one thread */
-    double atomic_acq_rel_ns;  /* dependent acquire-release atomicAdd, one word */
+                                  flight, one thread (least over the placements
+                                  of occ_link_ns) */
+    double atomic_acq_rel_ns;  /* dependent acquire-release atomicAdd, one word
+                                  (least over the same placements) */
     double occ_link_ns;        /* one uncontended link of the OCC commit chain as
                                   the execute kernel runs it (acquire version,
                                   CAS lock, acquire-release commit timestamp,
                                   one validation load, value store, release
                                   publish): the least time per committed
-                                  writer of one record */
+                                  writer of one record, least over eight
+                                  placements of the thread (the SMs of both
+                                  dies) */
+    double occ_link_max_ns;    /* the greatest over the same placements */
     double gather32_by_inflight_gbs[3]; /* random 32-byte sectors with 4, 8 and
                                   16 sectors in flight per thread */
     uint32_t gather32_best_inflight;    /* in-flight count of gather32_gbs */

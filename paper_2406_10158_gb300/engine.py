@@ -136,7 +136,8 @@ class MemoryProbe(ctypes.Structure):
                 ("sm_count", ctypes.c_uint32), ("contenders", ctypes.c_uint32),
                 ("lock_best_contenders", ctypes.c_uint32), ("occ_best_contenders", ctypes.c_uint32),
                 ("fence_ns", ctypes.c_double), ("atomic_acq_rel_ns", ctypes.c_double),
-                ("occ_link_ns", ctypes.c_double), ("gather32_by_inflight_gbs", ctypes.c_double * 3),
+                ("occ_link_ns", ctypes.c_double), ("occ_link_max_ns", ctypes.c_double),
+                ("gather32_by_inflight_gbs", ctypes.c_double * 3),
                 ("gather32_best_inflight", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 

@@ -41,6 +41,7 @@ def test_probe_figures_are_physical(built):
     assert m["atomic_acq_rel_ns"] > 0.5 * m["fence_ns"]
     assert m["occ_link_ns"] > m["atomic_acq_rel_ns"]
     assert m["occ_link_ns"] > m["l2_cas_ns"]
+    assert m["occ_link_max_ns"] >= m["occ_link_ns"]
 
 
 def test_execute_kernel_counts_its_atomics(built):
