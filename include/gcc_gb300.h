@@ -221,6 +221,19 @@ typedef struct gcc_exec_params {
                                   16; OCC: 64 -- an OCC abort nearly always
                                   means another transaction committed, so its
                                   retries rarely need queueing] */
+    uint32_t group_commit;     /* OCC on key-value databases: transactions per
+                                  commit unit, 2..8 (1 = off) [1].  The
+                                  batch's transactions are keyed by their
+                                  most-written record; a key's transactions
+                                  (in id order) form units that one lane group
+                                  attempts together: one lock per distinct
+                                  written record, consecutive commit
+                                  timestamps, per-member validation, writes
+                                  composed in timestamp order; members that
+                                  fail retry.  At most 255 ops per unit: the
+                                  unit size is cut to 255 / max_ops_per_txn */
+    uint32_t group_min_writes; /* writes in the batch that make a record a key
+                                  of units [32] */
     uint32_t reserved;         /* 0 */
 } gcc_exec_params;
 

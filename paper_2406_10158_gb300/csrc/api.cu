@@ -71,6 +71,8 @@ gcc_exec_params defaults() {
     p.queue_turn_ns = 1000;
     p.queue_width = 1;
     p.queue_after = 0;                   // per scheme, see queue_after_for
+    p.group_commit = 1;
+    p.group_min_writes = 32;
     return p;
 }
 
@@ -100,6 +102,8 @@ gcc_exec_params merged(const gcc_exec_params* in) {
     if (in->queue_turn_ns) p.queue_turn_ns = in->queue_turn_ns;
     if (in->queue_width) p.queue_width = in->queue_width;
     if (in->queue_after) p.queue_after = in->queue_after;
+    if (in->group_commit) p.group_commit = in->group_commit;
+    if (in->group_min_writes) p.group_min_writes = in->group_min_writes;
     return p;
 }
 
@@ -146,6 +150,8 @@ void free_db(gcc_db* db) {
     cudaFree(db->fold_flags);
     cudaFree(db->fold_seg);
     cudaFree(db->mv_slot);
+    cudaFree(db->unit_cnt);
+    cudaFree(db->unit_link);
     cudaFree(db->name_idx);
     cudaFree(db->name_last);
     cudaFree(db->ops_resolved);
@@ -247,6 +253,11 @@ gcc_status create_impl(const gcc_db_desc* desc, gcc_db** out) {
     if (d.schema == GCC_SCHEMA_KV &&
         (s = dev_alloc(&db->mv_slot, d.n_records * d.n_fields * 4, "version pointers")))
         return bail(s);
+    // OCC group commit: write counts per record and a link word per transaction
+    if (d.schema == GCC_SCHEMA_KV && d.n_records < 0xffffffffull &&
+        ((s = dev_alloc(&db->unit_cnt, d.n_records * 4, "group-commit write counts")) ||
+         (s = dev_alloc(&db->unit_link, d.max_batch_txns * 4, "group-commit links"))))
+        return bail(s);
     db->n_h_states = GCC_MAX_OUTSTANDING_BATCHES;
     if (cudaMallocHost(&db->h_states, sizeof(gcc::BatchState) * db->n_h_states) != cudaSuccess)
         return bail(fail(GCC_ERR_NOMEM, "cannot allocate pinned batch states"));
@@ -266,6 +277,7 @@ gcc_status validate_params(const gcc_exec_params& p) {
     if (p.warps_per_block == 0 || p.warps_per_block > 32)
         return fail(GCC_ERR_INVALID, "warps_per_block must be in 1..32");
     if (p.collapse > 2) return fail(GCC_ERR_INVALID, "collapse must be 0, 1 or 2");
+    if (p.group_commit > 8) return fail(GCC_ERR_INVALID, "group_commit must be in 0..8");
     if (p.retry_queue > 2) return fail(GCC_ERR_INVALID, "retry_queue must be 0, 1 or 2");
     if (p.det_dataflow > 2) return fail(GCC_ERR_INVALID, "det_dataflow must be 0, 1 or 2");
     return GCC_OK;
@@ -433,11 +445,25 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
                                 p.det_dataflow == 2));
         launches += 1 + 3 * ((bits + 7) / 8) + 1 + 3 + 1;   // emit, sort, flags, scan, need
     }
+    // OCC group commit on key-value batches: units of up to gu transactions
+    // (each unit's ops are staged together: at most 255 per unit)
+    const uint32_t gu = (scheme == GCC_OCC && kv && db->unit_link && p.group_commit >= 2)
+                            ? std::min<uint32_t>(p.group_commit, 255u / db->d.max_ops_per_txn)
+                            : 1u;
+    if (gu >= 2 && n_txns) {
+        a.unit_link = db->unit_link;
+        a.group_u = gu;
+        GCC_CK(gcc::occ_form_units(a, db->unit_cnt, db->sort, db->unit_link, gu,
+                                   p.group_min_writes, st));
+        launches += gcc::occ_form_units_launches(db->d.n_records);
+    }
     const int block = (int)p.warps_per_block * 32;
     const uint32_t slots = block / p.lanes_per_txn;
-    const size_t smem = (size_t)slots * db->d.max_ops_per_txn * gcc::STAGE_BYTES_PER_OP;
-    const int occ = kv ? gcc::kv_exec_occupancy(scheme, db->d.field_bytes, block, smem)
-                       : gcc::oe_exec_occupancy(scheme, block, smem);
+    const size_t smem = gu >= 2 ? (size_t)slots * gcc::occ_group_stage_bytes(gu, db->d.max_ops_per_txn)
+                                : (size_t)slots * db->d.max_ops_per_txn * gcc::STAGE_BYTES_PER_OP;
+    const int occ = gu >= 2 ? gcc::kv_occ_group_occupancy(db->d.field_bytes, block, smem)
+                    : kv    ? gcc::kv_exec_occupancy(scheme, db->d.field_bytes, block, smem)
+                            : gcc::oe_exec_occupancy(scheme, block, smem);
     if (occ <= 0)
         return fail(GCC_ERR_INVALID, "launch shape does not fit an SM (%d threads, %zu B shared)",
                     block, smem);
@@ -450,8 +476,11 @@ gcc_status execute_impl(gcc_db* db, gcc_scheme scheme, const gcc_txn* d_txns, ui
         GCC_CK(cudaMemsetAsync(db->rq, 0, (size_t)gcc::RETRY_QUEUES * 8, st));
 
     if (n_txns) {
-        GCC_CK(kv ? gcc::launch_kv_exec(scheme, db->d.field_bytes, a, (int)grid, block, smem, st)
-                  : gcc::launch_oe_exec(scheme, a, (int)grid, block, smem, st));
+        if (gu >= 2)
+            GCC_CK(gcc::launch_kv_occ_group(db->d.field_bytes, a, (int)grid, block, smem, st));
+        else
+            GCC_CK(kv ? gcc::launch_kv_exec(scheme, db->d.field_bytes, a, (int)grid, block, smem, st)
+                      : gcc::launch_oe_exec(scheme, a, (int)grid, block, smem, st));
         launches += 1;
     }
     GCC_CK(cudaEventRecord(rec.ev[2], st));

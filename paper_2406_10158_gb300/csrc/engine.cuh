@@ -322,6 +322,9 @@ struct ExecArgs {
     uint32_t* mv_field;
     ulonglong2* mv_val;
     uint32_t* mv_slot;           // per slot (field-major): its newest entry + 1
+    // OCC group commit (key-value): units of up to group_u transactions
+    const uint32_t* unit_link;   // per txn: next member | follower bit (null: off)
+    uint32_t group_u;
 };
 
 
@@ -338,6 +341,16 @@ constexpr uint32_t STAGE_BYTES_PER_OP = 8 + 8 + 16 + 16 + 8;
 cudaError_t launch_kv_exec(gcc_scheme scheme, uint32_t field_bytes, const ExecArgs& a,
                            int grid, int block, size_t smem, cudaStream_t s);
 int kv_exec_occupancy(gcc_scheme scheme, uint32_t field_bytes, int block, size_t smem);
+// OCC with group commit on key-value batches (occ_group.cu): unit formation,
+// staging bytes per lane group, launcher and occupancy.
+struct SortScratch;
+cudaError_t occ_form_units(const ExecArgs& a, uint32_t* cnt, SortScratch& s, uint32_t* link,
+                           uint32_t U, uint32_t min_writes, cudaStream_t st);
+uint32_t occ_form_units_launches(uint64_t n_records);
+size_t occ_group_stage_bytes(uint32_t U, uint32_t max_ops);
+cudaError_t launch_kv_occ_group(uint32_t field_bytes, const ExecArgs& a, int grid, int block,
+                                size_t smem, cudaStream_t s);
+int kv_occ_group_occupancy(uint32_t field_bytes, int block, size_t smem);
 // Order-entry execute kernel for one scheme.
 cudaError_t launch_oe_exec(gcc_scheme scheme, const ExecArgs& a, int grid, int block,
                            size_t smem, cudaStream_t s);

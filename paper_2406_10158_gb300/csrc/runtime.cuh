@@ -89,6 +89,8 @@ struct gcc_db {
     uint32_t* fold_flags = nullptr;     // deterministic fold: 2 words per transaction
     void* fold_seg = nullptr;           // deterministic fold: tile carries; MVCC values
     uint32_t* mv_slot = nullptr;        // MVCC: version pointer per key-value slot
+    uint32_t* unit_cnt = nullptr;       // OCC group commit: writes per record in the batch
+    uint32_t* unit_link = nullptr;      // OCC group commit: link word per transaction
     // order-entry: customers by (last, first, number) per district, and the
     // batch's ops with by-name payments resolved
     uint32_t* name_idx = nullptr;

@@ -49,6 +49,7 @@ class ExecParams(ctypes.Structure):
                 ("immediate_restart", ctypes.c_uint32), ("det_dataflow", ctypes.c_uint32),
                 ("retry_queue", ctypes.c_uint32), ("queue_turn_ns", ctypes.c_uint32),
                 ("queue_width", ctypes.c_uint32), ("queue_after", ctypes.c_uint32),
+                ("group_commit", ctypes.c_uint32), ("group_min_writes", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
 
 
