@@ -64,6 +64,8 @@ def parse_args(argv=None):
                         "order-entry warehouse counts")
     p.add_argument("--check", action="store_true",
                    help="sweep: replay every cell's batch on the CPU oracle (slow)")
+    p.add_argument("--sweep-parts", default="kv,hotspot,oe",
+                   help="sweep form: which parts to run (kv, hotspot, oe), comma-separated")
     p.add_argument("--n-db", type=int, default=64, help="batched form: databases")
     p.add_argument("--rates", default="1e5,1e6,1e7,1e8",
                    help="served form: offered rates (txn/s), comma-separated")
@@ -796,11 +798,46 @@ def replay_kv_cell(db, scheme, batch, tx, op, od, rs, rd, prm) -> bool:
     return bool(rep["ok"])
 
 
+def sweep_hotspot(args, rank, eng, wl, dev, up, prm, batch_ms):
+    """The sweep's hot-spot rows: uniform keys with 10% of the transactions
+    writing one record, under OCC and OCC with group commit (units of 8, one
+    unit per warp)."""
+    import torch
+    rows = []
+    table, batch = wl.kv_hotspot(args.seed + rank, hot_frac=0.1)
+    db = eng.Database("kv", n_records=1 << 24, n_fields=10, field_bytes=16,
+                      max_batch_txns=batch.n_txns, device=dev)
+    db.load_kv(table)
+    tx, op, od = up(batch.txns), up(batch.ops), up(batch.operands)
+    rs = torch.empty(batch.n_txns * 16, dtype=torch.uint8, device=dev)
+    rd = torch.empty(batch.n_ops * 16, dtype=torch.uint8, device=dev)
+    useful0 = algorithmic_bytes(batch)["bytes"]
+    gc = eng.params(deadline_ns=int(args.scheme_deadline_s * 1e9), group_commit=8,
+                    lanes_per_txn=32)
+    for name, p_s in (("occ", prm), ("occ-group8", gc)):
+        for _ in range(3):
+            db.execute("occ", tx, op, od, batch.n_txns, batch.n_ops, rs, rd, p_s)
+        hist = db.stage_history(2)
+        st = db.last_stats()
+        ms = statistics.mean(batch_ms(h) for h in hist)
+        row = {"workload": "hotspot", "scheme": name,
+               "committed_txn_per_s": st["committed"] / ms * 1e3,
+               "abort_rate": st["abort_rate"], "ms_per_batch": ms,
+               "algorithmic_gbs": useful0 / ms / 1e6,
+               "all_committed": st["committed"] == batch.n_txns}
+        if args.check:
+            row["replayed"] = replay_kv_cell(db, "occ", batch, tx, op, od, rs, rd, p_s)
+        rows.append(row)
+    db.close()
+    return rows
+
+
 def run_sweep(args, rank, world):
     """Committed txns/s and abort rate of every scheme on the key-value
     workload (2^24 x 10 x 16-byte slots, 2^20 txns x 16 ops) at Zipf theta in
-    {0, 0.6, 0.8, 0.99} x read ratio {0.5, 0.95}, and on the order-entry mix
-    (2^18 txns, 50/50 NewOrder/Payment) at W in {1, 8, 64}.  Batches are
+    {0, 0.6, 0.8, 0.99} x read ratio {0.5, 0.95}, of OCC with and without
+    group commit on a hot spot among cold records, and of every scheme on the
+    order-entry mix (2^18 txns, 50/50 NewOrder/Payment) at W in {1, 8, 64}.  Batches are
     device-resident; a batch's time is the sum of its stage events (control
     words, [deterministic preprocessing], execute, commit ranks)."""
     import torch
@@ -824,9 +861,10 @@ def run_sweep(args, rank, world):
     def batch_ms(h):
         return h["prep_ms"] + h["kernel_ms"] + h["order_ms"]
 
-    kv_rows, oe_rows = [], []
+    kv_rows, oe_rows, hot_rows = [], [], []
+    parts = set(args.sweep_parts.split(","))
     with ClockSampler(dev) as clocks:
-        for rr in (0.5, 0.95):
+        for rr in ((0.5, 0.95) if "kv" in parts else ()):
             for theta in (0.0, 0.6, 0.8, 0.99):
                 table, batch = wl.ycsb_kv(args.seed + rank, theta=theta, read_ratio=rr)
                 db = eng.Database("kv", n_records=1 << 24, n_fields=10, field_bytes=16,
@@ -856,7 +894,10 @@ def run_sweep(args, rank, world):
                                                          p_s)
                     kv_rows.append(row)
                 db.close()
-        for W in (1, 8, 64):
+        # one hot spot among cold records: OCC against OCC with group commit
+        for _ in range(1 if "hotspot" in parts else 0):
+            hot_rows += sweep_hotspot(args, rank, eng, wl, dev, up, prm, batch_ms)
+        for W in ((1, 8, 64) if "oe" in parts else ()):
             db0, batch, cap = wl.order_entry(W=W, n_txns=1 << 18)
             db = eng.Database("oe", n_warehouses=W, order_cap=cap, max_ops_per_txn=33,
                               max_batch_txns=batch.n_txns, max_batch_ops=batch.n_ops, device=dev)
@@ -889,16 +930,20 @@ def run_sweep(args, rank, world):
                         db.read_oe(), W, cap) == 0
                 oe_rows.append(row)
             db.close()
-    head = next(r for r in kv_rows if r["theta"] == 0.8 and r["read_ratio"] == 0.5
-                and r["scheme"] == "occ")
-    return {"metric": METRIC, "form": "sweep", "value": head["committed_txn_per_s"],
+    head = next((r for r in kv_rows if r["theta"] == 0.8 and r["read_ratio"] == 0.5
+                 and r["scheme"] == "occ"), None)
+    return {"metric": METRIC, "form": "sweep",
+            "value": head["committed_txn_per_s"] if head else None,
             "unit": "txn/s", "n_gpus": 1, "steps": 3, "warmup": 1, "ms_per_step": None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
             "config": {"workload": "kv 2^24 x 10 x 16 B, 2^20 txns x 16 ops, zipf {0,0.6,0.8,0.99}"
-                                   " x read ratio {0.5,0.95}; order-entry W {1,8,64}, 2^18 txns",
+                                   " x read ratio {0.5,0.95}; the same with uniform keys and 10%"
+                                   " of the txns writing one record (hotspot: occ, occ with"
+                                   " group commit); order-entry W {1,8,64}, 2^18 txns",
                        "value_is": "occ at zipf 0.8, read ratio 0.5"},
-            "kv": kv_rows, "order_entry": oe_rows, "clocks": clocks.summary()}
+            "kv": kv_rows, "hotspot": hot_rows, "order_entry": oe_rows,
+            "clocks": clocks.summary()}
 
 
 def main(argv=None):

@@ -331,6 +331,27 @@ def ycsb_kv(seed: int = SEEDS[1], *, theta: float = 0.8, read_ratio: float = 0.5
     return table, batch
 
 
+def kv_hotspot(seed: int = SEEDS[1], *, hot_frac: float = 0.1, nrec: int = 1 << 24,
+               n_txns: int = 1 << 20, nfields: int = 10, hot_key: int = 12345,
+               with_table: bool = True):
+    """The key-value shape of ``ycsb_kv`` with uniform keys (read ratio 0.5),
+    except that a ``hot_frac`` share of the transactions (drawn with their
+    own seed) turn their first op into an ADD on record ``hot_key``: one hot
+    spot among cold records.  Transactions that already touch ``hot_key``
+    are left as they are, so keys stay distinct within a transaction."""
+    table = kv_table_bytes(seed, nrec, nfields) if with_table else None
+    batch = kv_batch(derive_seed(seed, 7001), nrec=nrec, nfields=nfields, n_txns=n_txns,
+                     ops_per_txn=16, read_ratio=0.5, theta=0.0, field_bytes=16)
+    rng = np.random.default_rng(derive_seed(seed, 7002))
+    pick = np.nonzero(rng.random(n_txns) < hot_frac)[0]
+    keys = batch.ops["key"].reshape(n_txns, 16)
+    pick = pick[~(keys[pick] == hot_key).any(axis=1)]
+    first = batch.txns["first_op"][pick].astype(np.int64)
+    batch.ops["key"][first] = hot_key
+    batch.ops["kind"][first] = OP_ADD
+    return table, batch
+
+
 # ---------------------------------------------------------------------------
 # order-entry workloads (TPC-C-shaped NewOrder / Payment, Sec. IV-A)
 # ---------------------------------------------------------------------------

@@ -42,6 +42,18 @@ def test_nurand_range_and_read_ratio():
     assert not b.operands[b.ops["kind"] == wl.OP_READ].any()
 
 
+def test_hotspot_batch_shape():
+    _, b = wl.kv_hotspot(3, hot_frac=0.1, nrec=1 << 16, n_txns=4096, with_table=False)
+    keys = b.ops["key"].reshape(-1, 16)
+    assert all(len(set(r)) == 16 for r in keys)
+    hot = (keys == 12345)
+    writes = hot & (b.ops["kind"].reshape(-1, 16) == wl.OP_ADD)
+    share = hot.any(axis=1).mean()
+    assert 0.08 < share < 0.12
+    # the hot record is written by (nearly) every transaction that touches it
+    assert writes.sum() >= 0.95 * hot.sum()
+
+
 def test_order_entry_shapes():
     db, b, cap = wl.order_entry(seed=5, W=2, n_txns=2000)
     t = b.txns
