@@ -686,7 +686,9 @@ def run_served(args, rank, world):
     result on the host), against plain per-batch launches of the same requests
     (submit, wait, next).  Each rate runs min(--requests, 10 s of arrivals)
     requests -- 10 s or 10^7 requests at the default -- taken as a prefix of
-    one trace generated once."""
+    one trace generated once.  `value` is the highest committed rate;
+    `p99_latency_us` is the p99 at the highest offered rate the loop sustains
+    (98% of it committed), named in `p99_at_offered_txn_per_s`."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -763,6 +765,10 @@ def run_served(args, rank, world):
         dkv.close()
         doe.close()
     best = max(results, key=lambda r: r["committed_txn_per_s"])
+    # the latency figure of a serving system: at the highest offered rate it
+    # sustains (commits at least 98% of the offered rate), not at saturation
+    held = [r for r in results if r["committed_txn_per_s"] >= 0.98 * r["offered_txn_per_s"]]
+    sustained = max(held, key=lambda r: r["offered_txn_per_s"]) if held else best
     return {"metric": METRIC, "form": "served", "value": best["committed_txn_per_s"],
             "unit": "txn/s", "n_gpus": 1, "steps": len(rates), "warmup": 0,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -773,7 +779,8 @@ def run_served(args, rank, world):
                                    f"requests per rate",
                        "max_batch_txns": max_batch, "max_delay_us": 100, "depth": 4,
                        "trace_generation_s": round(gen_s, 1)},
-            "p99_latency_us": best["p99_latency_us"], "rates": results,
+            "p99_latency_us": sustained["p99_latency_us"],
+            "p99_at_offered_txn_per_s": sustained["offered_txn_per_s"], "rates": results,
             "plain_per_batch": {"value": committed / plain_s, "unit": "txn/s", "requests": m},
             "speedup_vs_plain": best["committed_txn_per_s"] / (committed / plain_s),
             "clocks": clocks.summary()}

@@ -513,9 +513,13 @@ gcc_status gcc_server_completions(gcc_server *s, gcc_completion *out, gcc_operan
 /* Open-loop replay of a request trace: request i (ops at
  * ops[txns[i].first_op ..]) arrives at start + arrival_offset_ns[i] for lane
  * lane_of[i]; the loop admits arrivals, launches and collects batches until
- * every request has completed.  Requests are admitted in index order, so
- * arrival_offset_ns should be nondecreasing.  out[i] and
- * reads_out[txns[i].first_op ..] receive the outcome of request i.
+ * every request has completed.  Each lane runs its own loop on its own host
+ * thread (a server with one lane runs on the calling thread); the call
+ * returns when every lane is done.  A lane admits its requests in index
+ * order, so arrival_offset_ns should be nondecreasing.  out[i] and
+ * reads_out[txns[i].first_op ..] receive the outcome of request i.  An error
+ * in a lane stops that lane; the call returns the lowest failing lane's
+ * status, its message prefixed by the lane.
  * GCC_ERR_INVALID (nothing run) for a bad lane or a request too large for its
  * lane, as in gcc_server_enqueue. */
 gcc_status gcc_server_run_trace(gcc_server *s, uint32_t n, const uint32_t *lane_of,

@@ -10,7 +10,10 @@
 //   d2h stream   : waits `exec`, results, read values and batch state back,
 //                  event `out`
 // so the next batch's upload overlaps the current execution, and lanes on
-// different databases execute concurrently.  Batches of one lane run in the
+// different databases execute concurrently.  A trace run gives every lane its
+// own host thread (admission, launches, completions), since at millions of
+// requests per second the host work per request, not the GPU, bounds one
+// thread; lanes share no state but the server's read-only parameters.  Batches of one lane run in the
 // order they were launched on its exec stream; a slot becomes free when its
 // `out` event has completed and its completions have been emitted.
 #include <algorithm>
@@ -18,6 +21,7 @@
 #include <cstring>
 #include <deque>
 #include <new>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -76,6 +80,7 @@ struct Lane {
     std::deque<Pending> backlog;
     uint64_t next_seq = 0;
     uint64_t committed = 0, aborts = 0, batches = 0;
+    uint64_t trace_done = 0;            // trace run: this lane's completions so far
 };
 
 }  // namespace
@@ -91,7 +96,6 @@ struct gcc_server {
     gcc_completion* trace_out = nullptr;
     gcc_operand* trace_reads = nullptr;
     const gcc_txn* trace_txns = nullptr;
-    uint64_t trace_done = 0;
 };
 
 namespace {
@@ -253,7 +257,7 @@ void emit(gcc_server* s, uint32_t li, Slot& sl, uint64_t t_done) {
             if (s->trace_reads)
                 std::memcpy(s->trace_reads + s->trace_txns[c.request].first_op, r,
                             sizeof(gcc_operand) * sl.h_txns[i].n_ops);
-            s->trace_done++;
+            s->lanes[li].trace_done++;
         } else {
             s->done.push_back(c);
             s->done_reads.emplace_back(r, r + sl.h_txns[i].n_ops);
@@ -261,9 +265,9 @@ void emit(gcc_server* s, uint32_t li, Slot& sl, uint64_t t_done) {
     }
 }
 
-gcc_status pump(gcc_server* s, bool flush_all) {
-    const uint64_t t = now_ns();
-    for (uint32_t li = 0; li < s->lanes.size(); ++li) {
+// Completions, backlog and a due launch of one lane.
+gcc_status pump_lane(gcc_server* s, uint32_t li, bool flush_all, uint64_t t) {
+    {
         Lane& l = s->lanes[li];
         // finished batches, in launch order
         while (!l.inflight.empty()) {
@@ -302,6 +306,15 @@ gcc_status pump(gcc_server* s, bool flush_all) {
                 if (st) return st;
             }
         }
+    }
+    return GCC_OK;
+}
+
+gcc_status pump(gcc_server* s, bool flush_all) {
+    const uint64_t t = now_ns();
+    for (uint32_t li = 0; li < s->lanes.size(); ++li) {
+        const gcc_status st = pump_lane(s, li, flush_all, t);
+        if (st) return st;
     }
     return GCC_OK;
 }
@@ -447,21 +460,48 @@ gcc_status gcc_server_run_trace(gcc_server* s, uint32_t n, const uint32_t* lane_
     s->trace_out = out;
     s->trace_reads = reads_out;
     s->trace_txns = txns;
-    s->trace_done = 0;
+    const uint32_t nl = (uint32_t)s->lanes.size();
+    std::vector<std::vector<uint32_t>> mine(nl);       // each lane's requests, in trace order
+    for (uint32_t i = 0; i < n; ++i) mine[lane_of[i]].push_back(i);
+    for (Lane& l : s->lanes) l.trace_done = 0;
+    std::vector<gcc_status> status(nl, GCC_OK);
+    std::vector<std::string> message(nl);
     const uint64_t t0 = now_ns();
-    uint32_t next = 0;
-    gcc_status st = GCC_OK;
-    while (!st && s->trace_done < n) {
-        const uint64_t now = now_ns() - t0;
-        while (!st && next < n && arrival_offset_ns[next] <= now) {
-            // the trace's arrays outlive the run: a parked request points into them
-            st = admit(s, lane_of[next], txns[next], ops + txns[next].first_op,
-                       operands + txns[next].first_op, t0 + arrival_offset_ns[next], next,
-                       true);
-            ++next;
+    auto run_lane = [&](uint32_t li) {
+        if (cudaSetDevice(s->device) != cudaSuccess) {
+            status[li] = GCC_ERR_CUDA;
+            message[li] = "cannot select device";
+            return;
         }
-        if (!st) st = pump(s, next == n);
+        const std::vector<uint32_t>& idx = mine[li];
+        const Lane& l = s->lanes[li];
+        size_t next = 0;
+        gcc_status st = GCC_OK;
+        while (!st && l.trace_done < idx.size()) {
+            const uint64_t now = now_ns() - t0;
+            while (!st && next < idx.size() && arrival_offset_ns[idx[next]] <= now) {
+                // the trace's arrays outlive the run: a parked request points into them
+                const uint32_t i = idx[next];
+                st = admit(s, li, txns[i], ops + txns[i].first_op, operands + txns[i].first_op,
+                           t0 + arrival_offset_ns[i], i, true);
+                ++next;
+            }
+            if (!st) st = pump_lane(s, li, next == idx.size(), now_ns());
+        }
+        status[li] = st;
+        if (st) message[li] = gcc_last_error();
+    };
+    if (nl == 1) {
+        run_lane(0);
+    } else {
+        std::vector<std::thread> workers;
+        workers.reserve(nl);
+        for (uint32_t li = 0; li < nl; ++li) workers.emplace_back(run_lane, li);
+        for (std::thread& w : workers) w.join();
     }
+    gcc_status st = GCC_OK;
+    for (uint32_t li = 0; li < nl && !st; ++li)
+        if (status[li]) st = fail(status[li], "lane %u: %s", li, message[li].c_str());
     s->trace_out = nullptr;
     s->trace_reads = nullptr;
     s->trace_txns = nullptr;
