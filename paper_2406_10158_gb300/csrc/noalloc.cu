@@ -20,7 +20,7 @@ constexpr uint32_t NA_MAX = 65536;   // records, ops and transactions per call
 
 // Byte layout of the static scratch (each piece 256-byte aligned).
 constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
-constexpr size_t NA_TILES = (NA_MAX + 2047) / 2048;     // radix-sort tiles of 2048 items
+constexpr size_t NA_TILES = (NA_MAX + 2047) / 2048;     // radix-sort tiles (of 2048 items or more)
 constexpr size_t OFF_META = 0;
 constexpr size_t OFF_K0 = OFF_META + align256(NA_MAX * 8);
 constexpr size_t OFF_V0 = OFF_K0 + align256(NA_MAX * 4);

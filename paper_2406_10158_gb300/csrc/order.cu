@@ -93,72 +93,74 @@ __global__ void rs_scan_rows(uint32_t* __restrict__ hist, uint32_t ntiles,
     if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
-// Stable scatter of one tile: rank every item among the tile's items with the
-// same digit, stage the tile in shared memory in digit order, then write each
-// digit's run to its global position with consecutive threads on consecutive
-// addresses (coalesced), instead of scattering single elements.
+// Stable scatter of one tile.  Each warp ranks its own contiguous run of
+// RS_CHUNKS * 32 items with warp-private digit counters (match_any groups the
+// lanes of one digit; no block barrier inside the loop); one digit-major
+// scan over (digit, warp) then gives every item its position in the tile
+// staged in digit order -- warp w's items of a digit follow warp w-1's, which
+// keeps the sort stable -- and each digit's run goes to its global position
+// with consecutive threads on consecutive addresses (coalesced).
 __global__ void __launch_bounds__(RS_BLOCK)
 rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, size_t n, int shift,
            const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals,
            uint32_t ntiles) {
     __shared__ uint32_t gbase[256];            // global start of each digit's run for this tile
-    __shared__ uint32_t lbase[256];            // start of each digit within the staged tile
-    __shared__ uint32_t cnt[256];              // items of each digit ranked so far
-    __shared__ uint32_t wcnt[RS_WARPS][256];   // per-warp digit counts of the current chunk
+    __shared__ uint32_t dstart[256];           // start of each digit within the staged tile
+    __shared__ uint32_t wc[RS_WARPS][256];     // per-warp digit counts, then per-warp starts
     __shared__ uint32_t skey[RS_TILE];
     __shared__ uint32_t sval[RS_TILE];
     __shared__ uint32_t warp_sums[32];
-    const int t = threadIdx.x, warp = t >> 5;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     gbase[t] = block_exclusive_scan<RS_WARPS>(totals[t], warp_sums, nullptr) +
                hist[(size_t)t * ntiles + blockIdx.x];
-    cnt[t] = 0;
-    for (int w = 0; w < RS_WARPS; ++w) wcnt[w][t] = 0;
+    for (int w = 0; w < RS_WARPS; ++w) wc[w][t] = 0;
     __syncthreads();
-    const size_t base = (size_t)blockIdx.x * RS_TILE;
+    const size_t tile0 = (size_t)blockIdx.x * RS_TILE;
+    const size_t base = tile0 + (size_t)warp * (RS_CHUNKS * 32);
     uint32_t key[RS_CHUNKS], val[RS_CHUNKS], rank[RS_CHUNKS];
 #pragma unroll
     for (int c = 0; c < RS_CHUNKS; ++c) {
-        const size_t i = base + (size_t)c * RS_BLOCK + t;
+        const size_t i = base + (size_t)c * 32 + lane;
         const bool valid = i < n;
         key[c] = valid ? kin[i] : 0u;
         val[c] = valid ? vin[i] : 0u;
+    }
+#pragma unroll
+    for (int c = 0; c < RS_CHUNKS; ++c) {
+        const bool valid = base + (size_t)c * 32 + lane < n;
         const uint32_t dg = valid ? (key[c] >> shift) & 255u : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, dg);
-        const uint32_t r = __popc(peers & lt_mask());
-        if (valid && r == 0) wcnt[warp][dg] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t run = cnt[t];
-            for (int w = 0; w < RS_WARPS; ++w) {
-                const uint32_t k = wcnt[w][t];
-                wcnt[w][t] = run;
-                run += k;
-            }
-            cnt[t] = run;
-        }
-        __syncthreads();
-        rank[c] = valid ? wcnt[warp][dg] + r : 0u;
-        __syncthreads();
-        for (int w = 0; w < RS_WARPS; ++w) wcnt[w][t] = 0;
-        __syncthreads();
+        const uint32_t prior = valid ? wc[warp][dg] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt_mask()) == 0) wc[warp][dg] = prior + __popc(peers);
+        __syncwarp();
+        rank[c] = prior + __popc(peers & lt_mask());
     }
-    lbase[t] = block_exclusive_scan<RS_WARPS>(cnt[t], warp_sums, nullptr);
+    __syncthreads();
+    uint32_t tot = 0;                          // thread t owns digit t
+    for (int w = 0; w < RS_WARPS; ++w) {
+        const uint32_t x = wc[w][t];
+        wc[w][t] = tot;
+        tot += x;
+    }
+    dstart[t] = block_exclusive_scan<RS_WARPS>(tot, warp_sums, nullptr);
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < RS_CHUNKS; ++c) {
-        if (base + (size_t)c * RS_BLOCK + t < n) {
-            const uint32_t pos = lbase[(key[c] >> shift) & 255u] + rank[c];
+        if (base + (size_t)c * 32 + lane < n) {
+            const uint32_t dg = (key[c] >> shift) & 255u;
+            const uint32_t pos = dstart[dg] + wc[warp][dg] + rank[c];
             skey[pos] = key[c];
             sval[pos] = val[c];
         }
     }
     __syncthreads();
-    const uint32_t tile_n = (uint32_t)((n - base) < (size_t)RS_TILE ? (n - base) : RS_TILE);
+    const uint32_t tile_n = (uint32_t)((n - tile0) < (size_t)RS_TILE ? (n - tile0) : RS_TILE);
     for (uint32_t i = t; i < tile_n; i += RS_BLOCK) {
         const uint32_t k = skey[i];
         const uint32_t dg = (k >> shift) & 255u;
-        const uint32_t out = gbase[dg] + (i - lbase[dg]);
+        const uint32_t out = gbase[dg] + (i - dstart[dg]);
         kout[out] = k;
         vout[out] = sval[i];
     }
