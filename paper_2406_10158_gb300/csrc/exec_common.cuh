@@ -582,20 +582,24 @@ __device__ int tictoc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, 
 // batch ends (launch_mv_flatten).  Concurrency control is per record, in the
 // record's head word (engine.cuh): newest version's wts and rts, and a
 // pending writer.
-//  * Write at ts: needs no pending writer, wts < ts and rts <= ts; installs
-//    itself as the pending writer by a CAS and reads its slot's newest
-//    version (the pointer's entry, or the table slot) -- no other writer can
-//    add one while it is pending.
+//  * Write at ts: needs no pending writer, wts < ts and rts <= ts; reads its
+//    slot's newest version (the pointer's entry, or the table slot) and then
+//    installs itself as the pending writer by a CAS from the head it read:
+//    if the CAS succeeds, no writer became pending or committed since that
+//    head, so the version read is still the newest, and none can add one
+//    while it is pending.
 //  * Read at ts: aborts if an older writer is pending (its version might be
 //    the one to read); if the record's newest version is older than ts it
 //    raises the head's rts to ts by a CAS, so that no writer older than ts can
 //    add a version under it; it then walks its slot's entries from the newest
 //    to the first older than ts (newer ones, from writers after ts, are
 //    stepped over), or takes the table slot.
-//  * Commit: the new entries go into the store, then (release) the slots'
+//  * Commit: the new entries go into the store (a range of it taken once per
+//    transaction, before its first attempt), then (release) the slots'
 //    version pointers, then (release) each head is set to (ts, ts, no writer)
-//    by a CAS loop -- only readers' rts raises, all below ts, can move it
-//    meanwhile.  Abort: the pending marks are withdrawn the same way.
+//    by a CAS loop that starts from the head this writer installed -- only
+//    readers' rts raises, all below ts, can move it meanwhile.  Abort: the
+//    pending marks are withdrawn the same way.
 // Versions are stored when the writer commits, so an aborted attempt leaves
 // nothing to undo but its pending marks (the paper's version pointers are
 // likewise updated at commit).  Commit order: the timestamp, batch-relative
@@ -638,8 +642,9 @@ __device__ __forceinline__ bool mv_version(const ExecArgs& a, uint64_t d, uint32
 // reader attempt, so the loop ends; it is bounded all the same, and a word
 // still not updated after 2^24 tries sets GCC_DEVERR_DEADLINE.
 __device__ __forceinline__ void mv_set_head(const ExecArgs& a, ulonglong2* m, bool commit,
-                                            uint32_t ts, uint32_t& n_atom) {
-    ulonglong2 cur = ld128_acquire(m);
+                                            uint32_t ts, uint64_t installed, uint32_t& n_atom) {
+    // first guess: the head as this writer installed it (wts|rts, pending ts)
+    ulonglong2 cur = make_ulonglong2(installed, mv_pack(ts, 0u));
     for (uint32_t tries = 0;; ++tries) {
         if (tries >= (1u << 24)) {
             atomicOr(&a.st->error, GCC_DEVERR_DEADLINE);
@@ -659,11 +664,34 @@ __device__ __forceinline__ void mv_set_head(const ExecArgs& a, ulonglong2* m, bo
     }
 }
 
+// The transaction's range of the version store, taken once before its first
+// attempt: lane i's write ops take the entries after those of the lanes
+// before it.  Returns the lane's first entry.
+template <class Work>
+__device__ __forceinline__ uint32_t mv_entries(const ExecArgs& a, const Lane& L, const Stage& S,
+                                               uint32_t nops, uint32_t& base) {
+    uint32_t mine = 0;
+    for (uint32_t j = L.lig; j < nops; j += L.G) mine += Work::writes(S.desc[j]) ? 1u : 0u;
+    uint32_t incl = mine;                                   // inclusive scan over the group
+    for (uint32_t off = 1; off < L.G; off <<= 1) {
+        const uint32_t v = __shfl_up_sync(L.gmask, incl, off, L.G);
+        if (L.lig >= off) incl += v;
+    }
+    if (base == NO_CC) {
+        const uint32_t total = __shfl_sync(L.gmask, incl, L.gbase + L.G - 1);
+        unsigned long long b = 0;
+        if (L.lig == 0 && total) { b = atomicAdd(&a.st->mv_used, (unsigned long long)total); ++L.n_atom; }
+        base = (uint32_t)__shfl_sync(L.gmask, b, L.gbase);
+    }
+    return base + incl - mine;
+}
+
 template <class Work>
 __device__ int mvcc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint32_t t,
                             uint64_t first, uint32_t nops, uint32_t attempt,
-                            unsigned long long& order_key, uint32_t& crec) {
+                            unsigned long long& order_key, uint32_t& crec, uint32_t& mv_base) {
     const uint32_t kmax = (nops + L.G - 1) / L.G;
+    uint32_t e = mv_entries<Work>(a, L, S, nops, mv_base);
     const unsigned long long t64 = group_ticket(L, &a.st->ticket) + 1;
     if (t64 >= 0xFFFFFFFFull) {
         if (L.lig == 0) atomicOr(&a.st->error, GCC_DEVERR_TS_OVERFLOW);
@@ -701,6 +729,13 @@ __device__ int mvcc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, ui
                     const ulonglong2 h = ld128_acquire(m);
                     const uint32_t wts = mv_lo(h.x), rts = mv_hi(h.x), pend = mv_lo(h.y);
                     if (pend != 0 || wts >= ts || rts > ts) { ok = false; break; }
+                    // the slot's newest version, before the pending mark: its
+                    // pointer's entry or the table slot (every committed
+                    // version is older than ts); still the newest if the CAS
+                    // from h succeeds
+                    uint32_t pe;
+                    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(pe) : "l"(mv_slot_ptr(a, d)) : "memory");
+                    const ulonglong2 v = pe ? ld_slot16(a.mv_val + (pe - 1)) : Work::load(a, d);
                     ++L.n_atom;
                     const ulonglong2 o = cas128_acquire(m, h, make_ulonglong2(h.x, mv_pack(ts, mv_hi(h.y))));
                     if (o.x != h.x || o.y != h.y) {
@@ -708,12 +743,8 @@ __device__ int mvcc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, ui
                         continue;
                     }
                     held |= 1ull << k;
-                    // the slot's newest version: its pointer's entry or the
-                    // table slot (every committed version is older than ts)
-                    uint32_t e;
-                    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(e) : "l"(mv_slot_ptr(a, d)) : "memory");
-                    const ulonglong2 v = e ? ld_slot16(a.mv_val + (e - 1)) : Work::load(a, d);
-                    S.obs[j] = e;                               // the entry it supersedes
+                    S.obs[j] = pe;                              // the entry it supersedes
+                    S.aux[j] = h.x;                             // the head's first word as installed
                     S.oldv[j] = v;
                     S.newv[j] = Work::compute(a, d, v, a.operands[first + j]);
                     break;
@@ -725,19 +756,7 @@ __device__ int mvcc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, ui
     }
     fail = __any_sync(L.gmask, fail) || injected_abort(a, t, attempt);
     if (!fail) {
-        // one range of the version store for the group's writes: lane i's
-        // entries follow those of the lanes before it
-        const uint32_t mine = (uint32_t)__popcll(held);
-        uint32_t incl = mine;                                   // inclusive scan over the group
-        for (uint32_t off = 1; off < L.G; off <<= 1) {
-            const uint32_t v = __shfl_up_sync(L.gmask, incl, off, L.G);
-            if (L.lig >= off) incl += v;
-        }
-        const uint32_t total = __shfl_sync(L.gmask, incl, L.gbase + L.G - 1);
-        unsigned long long base = 0;
-        if (L.lig == 0 && total) { base = atomicAdd(&a.st->mv_used, (unsigned long long)total); ++L.n_atom; }
-        base = __shfl_sync(L.gmask, base, L.gbase);
-        uint32_t e = (uint32_t)base + incl - mine;
+        // every write op holds its record now: the lane's entries, in op order
         for (uint32_t k = 0; k < kmax; ++k)
             if (held >> k & 1) {
                 const uint32_t j = L.lig + k * L.G;
@@ -762,15 +781,19 @@ __device__ int mvcc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, ui
                 }
             fence_acq_rel();
             for (uint32_t k = 0; k < kmax; ++k)
-                if (held >> k & 1)
-                    mv_set_head(a, heads + Work::rec(a, S.desc[L.lig + k * L.G]), true, ts, L.n_atom);
+                if (held >> k & 1) {
+                    const uint32_t j = L.lig + k * L.G;
+                    mv_set_head(a, heads + Work::rec(a, S.desc[j]), true, ts, S.aux[j], L.n_atom);
+                }
         }
         order_key = ts;
         return COMMIT;
     }
     for (uint32_t k = 0; k < kmax; ++k)
-        if (held >> k & 1)
-            mv_set_head(a, heads + Work::rec(a, S.desc[L.lig + k * L.G]), false, ts, L.n_atom);
+        if (held >> k & 1) {
+            const uint32_t j = L.lig + k * L.G;
+            mv_set_head(a, heads + Work::rec(a, S.desc[j]), false, ts, S.aux[j], L.n_atom);
+        }
     crec = group_conflict(L, frec);
     return ABORT;
 }
@@ -935,6 +958,7 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
     uint64_t wake = 0;            // global-timer time before which the group waits
     uint32_t qi = NO_Q, qt = 0;   // retry queue and ticket while queued
     uint32_t pq = NO_Q;           // queue to join once the backoff is over
+    uint32_t mv_base = NO_CC;     // MVCC: the transaction's version-store range
     uint64_t first = 0;
     const ExecArgs* A = nullptr;
 
@@ -990,6 +1014,7 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
                     has = true;
                     attempts = 0;
                     wake = 0;
+                    mv_base = NO_CC;
                 }
                 __syncwarp(L.gmask);
             }
@@ -1058,7 +1083,7 @@ __device__ void group_loop(Fetch& F, const Lane& L, const Stage& S, uint32_t M, 
                                                    seq, crec);
                 else if constexpr (SCHEME == GCC_MVCC)
                     outcome = mvcc_attempt<Work>(a, L, S, t, first, nops, attempts, order_key,
-                                                 crec);
+                                                 crec, mv_base);
                 else
                     outcome = det_attempt<Work>(a, L, S, t, first, nops, order_key);
             } else if (L.lig == 0) {

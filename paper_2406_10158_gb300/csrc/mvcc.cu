@@ -8,8 +8,8 @@
 // its slot's newest (the slot's version pointer names it); if so it writes
 // its value into the table slot and clears the pointer.  The record heads are
 // then zeroed, so the next batch starts from one version per slot, no
-// pointers and empty heads.  Work: one pass over the entries (one per
-// committed write) and one over the heads.
+// pointers and empty heads.  Work: one pass over the entries (one per write
+// of a transaction that attempted) and one over the heads.
 #include "engine.cuh"
 
 namespace gcc {
@@ -20,7 +20,11 @@ __global__ void mv_flatten_kernel(const __grid_constant__ ExecArgs a) {
     const unsigned long long used = a.st->mv_used;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < used; i += stride) {
+        // a transaction that gave up left its range of entries unwritten
+        // (stale scratch): no version pointer names them, but their record
+        // and field must be checked before they are used as an index
         const uint32_t r = a.mv_rec[i], f = a.mv_field[i];
+        if (r >= a.n_records || f >= a.n_fields) continue;
         uint32_t* p = a.mv_slot + (uint64_t)f * a.n_records + r;
         if (*p != i + 1) continue;                 // an older version of its slot
         uint8_t* slot = a.table + ((uint64_t)f * a.n_records + r) * FB;
