@@ -612,22 +612,27 @@ __device__ __forceinline__ uint32_t* mv_slot_ptr(const ExecArgs& a, uint64_t d) 
     return a.mv_slot + (uint64_t)op_field(d) * a.n_records + op_key(d);
 }
 
-// The newest version of op d's slot older than ts: its entries from the
-// newest (version pointer, read with acquire) down, else the table slot.
-// False when the walk would step over more than MV_WALK_MAX entries (the
-// attempt then aborts).
-template <class Work>
-__device__ __forceinline__ bool mv_version(const ExecArgs& a, uint64_t d, uint32_t ts,
-                                           ulonglong2& out) {
+__device__ __forceinline__ uint32_t mv_pointer(const ExecArgs& a, uint64_t d) {
     uint32_t e;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(e) : "l"(mv_slot_ptr(a, d)) : "memory");
+    return e;
+}
+
+// The newest version of op d's slot older than ts: its entries from the
+// newest (version pointer e, read with acquire) down, else the table slot.
+// An entry's value is loaded beside its timestamp.  False when the walk would
+// step over more than MV_WALK_MAX entries (the attempt then aborts).
+template <class Work>
+__device__ __forceinline__ bool mv_version(const ExecArgs& a, uint64_t d, uint32_t ts, uint32_t e,
+                                           ulonglong2& out) {
     for (uint32_t n = 0; e != 0; ++n) {
         if (n >= MV_WALK_MAX) return false;
         const uint32_t i = e - 1;
         const uint32_t wts = ld_relaxed_u32(a.mv_wts + i);
         const uint32_t nxt = ld_relaxed_u32(a.mv_next + i);
+        const ulonglong2 v = ld_slot16(a.mv_val + i);
         if (wts < ts) {
-            out = ld_slot16(a.mv_val + i);
+            out = v;
             return true;
         }
         e = nxt;
@@ -714,12 +719,16 @@ __device__ int mvcc_attempt(const ExecArgs& a, const Lane& L, const Stage& S, ui
                     const ulonglong2 h = ld128_acquire(m);
                     const uint32_t wts = mv_lo(h.x), rts = mv_hi(h.x), pend = mv_lo(h.y);
                     if (pend != 0 && pend < ts) break;          // an older writer is pending
+                    // the version pointer beside the rts raise: if the CAS
+                    // from h succeeds, no version older than ts was added
+                    // after h (its writer would have changed the head first)
+                    const uint32_t pe = mv_pointer(a, d);
                     if (wts < ts && rts < ts) {
                         ++L.n_atom;
                         const ulonglong2 o = cas128_acquire(m, h, make_ulonglong2(mv_pack(wts, ts), h.y));
                         if (o.x != h.x || o.y != h.y) continue;
                     }
-                    ok = mv_version<Work>(a, d, ts, S.oldv[j]);
+                    ok = mv_version<Work>(a, d, ts, pe, S.oldv[j]);
                     break;
                 }
                 if (!ok) { fail = true; frec = r; }
