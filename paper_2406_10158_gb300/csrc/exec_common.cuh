@@ -356,12 +356,19 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
                     if (tries >= a.read_retries) { fail = true; frec = r; break; }
                 }
             } else {
-                // write: needs ts > RTS and ts > WTS; mark dirty with WTS = ts
+                // write: needs ts > RTS and ts > WTS; mark dirty with WTS = ts.
+                // The value is read before the mark, after the word (with
+                // acquire): values change only while a word is dirty, and a
+                // writer that marked it since changed the word, so the value
+                // belongs to w if the CAS from w succeeds -- the load then lies
+                // outside the record's tenure.
                 ulonglong2* m = words + r;
                 bool ok = !collapse_loser(a, r);
+                ulonglong2 v = make_ulonglong2(0ull, 0ull);
                 for (uint32_t tries = 0; ok; ++tries) {
-                    const ulonglong2 w = ld_slot16(m);
+                    const ulonglong2 w = ld128_acquire(m);
                     if ((w.y & TO_DIRTY) || ts < w.x || ts < w.y) { ok = false; break; }
+                    v = Work::load(a, d);
                     ++L.n_atom;
                     const ulonglong2 o = cas128_acquire(m, w, make_ulonglong2(w.x, TO_DIRTY | ts));
                     if (o.x == w.x && o.y == w.y) { S.obs[j] = w.y; break; }
@@ -369,7 +376,6 @@ __device__ int to_attempt(const ExecArgs& a, const Lane& L, const Stage& S, uint
                 }
                 if (ok) {
                     held |= 1ull << k;
-                    const ulonglong2 v = Work::load(a, d);
                     S.oldv[j] = v;
                     S.newv[j] = Work::compute(a, d, v, a.operands[first + j]);
                 } else {
