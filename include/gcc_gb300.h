@@ -513,9 +513,9 @@ gcc_status gcc_server_completions(gcc_server *s, gcc_completion *out, gcc_operan
 /* Open-loop replay of a request trace: request i (ops at
  * ops[txns[i].first_op ..]) arrives at start + arrival_offset_ns[i] for lane
  * lane_of[i]; the loop admits arrivals, launches and collects batches until
- * every request has completed.  Each lane runs its own loop on its own host
- * thread (a server with one lane runs on the calling thread); the call
- * returns when every lane is done.  A lane admits its requests in index
+ * every request has completed.  Each lane runs on two host threads of its
+ * own, one admitting arrivals and launching batches, one collecting finished
+ * batches; the call returns when every lane is done.  A lane admits its requests in index
  * order, so arrival_offset_ns should be nondecreasing.  out[i] and
  * reads_out[txns[i].first_op ..] receive the outcome of request i.  An error
  * in a lane stops that lane; the call returns the lowest failing lane's

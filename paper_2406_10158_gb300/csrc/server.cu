@@ -10,10 +10,13 @@
 //   d2h stream   : waits `exec`, results, read values and batch state back,
 //                  event `out`
 // so the next batch's upload overlaps the current execution, and lanes on
-// different databases execute concurrently.  A trace run gives every lane its
-// own host thread (admission, launches, completions), since at millions of
-// requests per second the host work per request, not the GPU, bounds one
-// thread; lanes share no state but the server's read-only parameters.  Batches of one lane run in the
+// different databases execute concurrently.  A trace run gives every lane two
+// host threads -- a feeder (admission, batch forming, launches) and a
+// completer (finished batches, completions, freeing slots) -- since at
+// millions of requests per second the host work per request, not the GPU,
+// bounds one thread.  They hand slots over through each slot's state word and
+// a ring of launched slots (release/acquire); lanes share no state but the
+// server's read-only parameters.  Batches of one lane run in the
 // order they were launched on its exec stream; a slot becomes free when its
 // `out` event has completed and its completions have been emitted.
 #include <algorithm>
@@ -55,8 +58,13 @@ struct Slot {
     uint32_t n_txns = 0;
     uint64_t n_ops = 0, write_bytes = 0, seq = 0, oldest = 0;
     std::vector<uint64_t> req, arrival;
-    SlotState state = FREE;
+    int state = FREE;                   // SlotState; read and written atomically
 };
+
+// A slot's state is the hand-off between a lane's feeder (FREE -> FORMING ->
+// INFLIGHT) and its completer (INFLIGHT -> FREE): release stores, acquire loads.
+int state_of(const Slot& sl) { return __atomic_load_n(&sl.state, __ATOMIC_ACQUIRE); }
+void set_state(Slot& sl, int st) { __atomic_store_n(&sl.state, st, __ATOMIC_RELEASE); }
 
 // A request waiting for a free slot.  Requests of a trace point into the
 // trace's arrays, which outlive the run; requests enqueued one by one own a
@@ -76,7 +84,10 @@ struct Lane {
     cudaStream_t h2d = nullptr, exec = nullptr, d2h = nullptr;
     std::vector<Slot> slots;
     int forming = -1;
-    std::deque<int> inflight;
+    // launched slots in launch order: a ring written by the feeder (tail) and
+    // read by the completer (head), depth <= 8 entries
+    int ring[8] = {0};
+    uint32_t head = 0, tail = 0;
     std::deque<Pending> backlog;
     uint64_t next_seq = 0;
     uint64_t committed = 0, aborts = 0, batches = 0;
@@ -132,8 +143,7 @@ gcc_status launch(gcc_server* s, Lane& l) {
     Slot& sl = l.slots[l.forming];
     l.forming = -1;
     sl.seq = l.next_seq++;
-    sl.state = INFLIGHT;
-    l.inflight.push_back((int)(&sl - l.slots.data()));
+    set_state(sl, INFLIGHT);
     const uint64_t tb = (uint64_t)sl.n_txns * sizeof(gcc_txn), ob = sl.n_ops * sizeof(gcc_op),
                    pb = sl.n_ops * sizeof(gcc_operand);
     cudaError_t e = cudaSuccess;
@@ -157,14 +167,23 @@ gcc_status launch(gcc_server* s, Lane& l) {
     if (!e && sl.n_ops) e = cudaMemcpyAsync(sl.h_reads, sl.d_reads, pb, cudaMemcpyDeviceToHost, l.d2h);
     if (!e) e = cudaEventRecord(sl.ev_out, l.d2h);
     if (e) return fail(GCC_ERR_CUDA, "server download: %s", cudaGetErrorString(e));
+    // into the ring only once its last event is recorded: the completer
+    // queries that event, and an event never recorded reads as complete
+    const uint32_t t = __atomic_load_n(&l.tail, __ATOMIC_RELAXED);
+    l.ring[t % 8] = (int)(&sl - l.slots.data());
+    __atomic_store_n(&l.tail, t + 1, __ATOMIC_RELEASE);
     return GCC_OK;
+}
+
+bool ring_empty(const Lane& l) {
+    return __atomic_load_n(&l.head, __ATOMIC_ACQUIRE) == __atomic_load_n(&l.tail, __ATOMIC_ACQUIRE);
 }
 
 int take_free(Lane& l) {
     for (size_t i = 0; i < l.slots.size(); ++i)
-        if (l.slots[i].state == FREE) {
+        if (state_of(l.slots[i]) == FREE) {
             Slot& sl = l.slots[i];
-            sl.state = FORMING;
+            set_state(sl, FORMING);
             sl.n_txns = 0;
             sl.n_ops = 0;
             sl.write_bytes = 0;
@@ -257,57 +276,68 @@ void emit(gcc_server* s, uint32_t li, Slot& sl, uint64_t t_done) {
             if (s->trace_reads)
                 std::memcpy(s->trace_reads + s->trace_txns[c.request].first_op, r,
                             sizeof(gcc_operand) * sl.h_txns[i].n_ops);
-            s->lanes[li].trace_done++;
         } else {
             s->done.push_back(c);
             s->done_reads.emplace_back(r, r + sl.h_txns[i].n_ops);
         }
     }
+    if (s->trace_out) __atomic_fetch_add(&s->lanes[li].trace_done, (uint64_t)sl.n_txns, __ATOMIC_RELEASE);
 }
 
-// Completions, backlog and a due launch of one lane.
-gcc_status pump_lane(gcc_server* s, uint32_t li, bool flush_all, uint64_t t) {
-    {
-        Lane& l = s->lanes[li];
-        // finished batches, in launch order
-        while (!l.inflight.empty()) {
-            Slot& sl = l.slots[l.inflight.front()];
-            const cudaError_t q = cudaEventQuery(sl.ev_out);
-            if (q == cudaErrorNotReady) break;
-            if (q != cudaSuccess) return fail(GCC_ERR_CUDA, "batch failed: %s", cudaGetErrorString(q));
-            emit(s, li, sl, now_ns());
-            l.committed += sl.h_state->committed;
-            l.aborts += sl.h_state->aborts;
-            l.batches++;
-            sl.state = FREE;
-            l.inflight.pop_front();
+// Finished batches of one lane, in launch order: their completions are
+// emitted and their slots freed (the lane's completer).
+gcc_status lane_collect(gcc_server* s, uint32_t li) {
+    Lane& l = s->lanes[li];
+    while (!ring_empty(l)) {
+        const uint32_t h = __atomic_load_n(&l.head, __ATOMIC_RELAXED);
+        Slot& sl = l.slots[l.ring[h % 8]];
+        const cudaError_t q = cudaEventQuery(sl.ev_out);
+        if (q == cudaErrorNotReady) break;
+        if (q != cudaSuccess) return fail(GCC_ERR_CUDA, "batch failed: %s", cudaGetErrorString(q));
+        emit(s, li, sl, now_ns());
+        l.committed += sl.h_state->committed;
+        l.aborts += sl.h_state->aborts;
+        l.batches++;
+        set_state(sl, FREE);
+        __atomic_store_n(&l.head, h + 1, __ATOMIC_RELEASE);
+    }
+    return GCC_OK;
+}
+
+// Backlog into free slots and a due launch of one lane (the lane's feeder).
+gcc_status lane_feed(gcc_server* s, uint32_t li, bool flush_all, uint64_t t) {
+    Lane& l = s->lanes[li];
+    while (!l.backlog.empty()) {
+        if (l.forming < 0) l.forming = take_free(l);
+        if (l.forming < 0) break;
+        Pending& p = l.backlog.front();
+        const gcc_op* pops = ops_of(p);
+        uint64_t wbytes = 0;
+        for (uint32_t j = 0; j < p.txn.n_ops; ++j) wbytes += writes(pops[j].kind) ? 16 : 0;
+        if (!fits(l, l.slots[l.forming], p.txn.n_ops, wbytes)) {
+            gcc_status st = launch(s, l);
+            if (st) return st;
+            continue;
         }
-        // backlog into free slots
-        while (!l.backlog.empty()) {
-            if (l.forming < 0) l.forming = take_free(l);
-            if (l.forming < 0) break;
-            Pending& p = l.backlog.front();
-            const gcc_op* pops = ops_of(p);
-            uint64_t wbytes = 0;
-            for (uint32_t j = 0; j < p.txn.n_ops; ++j) wbytes += writes(pops[j].kind) ? 16 : 0;
-            if (!fits(l, l.slots[l.forming], p.txn.n_ops, wbytes)) {
-                gcc_status st = launch(s, l);
-                if (st) return st;
-                continue;
-            }
-            append(l.slots[l.forming], p.txn, pops, opd_of(p), wbytes, p.arrival, p.id);
-            l.backlog.pop_front();
-        }
-        // a forming batch past its delay (or everything, when draining) launches
-        if (l.forming >= 0) {
-            Slot& sl = l.slots[l.forming];
-            if (sl.n_txns && (flush_all || t - sl.oldest >= l.cfg.max_delay_ns)) {
-                gcc_status st = launch(s, l);
-                if (st) return st;
-            }
+        append(l.slots[l.forming], p.txn, pops, opd_of(p), wbytes, p.arrival, p.id);
+        l.backlog.pop_front();
+    }
+    // a forming batch past its delay (or everything, when draining) launches
+    if (l.forming >= 0) {
+        Slot& sl = l.slots[l.forming];
+        if (sl.n_txns && (flush_all || t - sl.oldest >= l.cfg.max_delay_ns)) {
+            gcc_status st = launch(s, l);
+            if (st) return st;
         }
     }
     return GCC_OK;
+}
+
+// Completions, backlog and a due launch of one lane, on one thread.
+gcc_status pump_lane(gcc_server* s, uint32_t li, bool flush_all, uint64_t t) {
+    gcc_status st = lane_collect(s, li);
+    if (!st) st = lane_feed(s, li, flush_all, t);
+    return st;
 }
 
 gcc_status pump(gcc_server* s, bool flush_all) {
@@ -321,7 +351,7 @@ gcc_status pump(gcc_server* s, bool flush_all) {
 
 bool idle(const gcc_server* s) {
     for (const Lane& l : s->lanes)
-        if (!l.inflight.empty() || !l.backlog.empty() ||
+        if (!ring_empty(l) || !l.backlog.empty() ||
             (l.forming >= 0 && l.slots[l.forming].n_txns))
             return false;
     return true;
@@ -464,20 +494,29 @@ gcc_status gcc_server_run_trace(gcc_server* s, uint32_t n, const uint32_t* lane_
     std::vector<std::vector<uint32_t>> mine(nl);       // each lane's requests, in trace order
     for (uint32_t i = 0; i < n; ++i) mine[lane_of[i]].push_back(i);
     for (Lane& l : s->lanes) l.trace_done = 0;
-    std::vector<gcc_status> status(nl, GCC_OK);
-    std::vector<std::string> message(nl);
+    // two threads per lane: the feeder admits arrivals, forms and launches
+    // batches; the completer collects finished batches and frees their
+    // slots.  An error on either stops both threads of its lane.
+    std::vector<gcc_status> status(2 * nl, GCC_OK);
+    std::vector<std::string> message(2 * nl);
+    std::vector<int> stop(nl, 0);
     const uint64_t t0 = now_ns();
-    auto run_lane = [&](uint32_t li) {
+    auto stopped = [&](uint32_t li) { return __atomic_load_n(&stop[li], __ATOMIC_ACQUIRE) != 0; };
+    auto halt = [&](uint32_t li, uint32_t w, gcc_status st) {
+        status[w] = st;
+        message[w] = gcc_last_error();
+        __atomic_store_n(&stop[li], 1, __ATOMIC_RELEASE);
+    };
+    auto feeder = [&](uint32_t li) {
         if (cudaSetDevice(s->device) != cudaSuccess) {
-            status[li] = GCC_ERR_CUDA;
-            message[li] = "cannot select device";
+            halt(li, 2 * li, fail(GCC_ERR_CUDA, "cannot select device"));
             return;
         }
         const std::vector<uint32_t>& idx = mine[li];
         const Lane& l = s->lanes[li];
         size_t next = 0;
         gcc_status st = GCC_OK;
-        while (!st && l.trace_done < idx.size()) {
+        while (!st && !stopped(li)) {
             const uint64_t now = now_ns() - t0;
             while (!st && next < idx.size() && arrival_offset_ns[idx[next]] <= now) {
                 // the trace's arrays outlive the run: a parked request points into them
@@ -486,22 +525,37 @@ gcc_status gcc_server_run_trace(gcc_server* s, uint32_t n, const uint32_t* lane_
                            t0 + arrival_offset_ns[i], i, true);
                 ++next;
             }
-            if (!st) st = pump_lane(s, li, next == idx.size(), now_ns());
+            if (!st) st = lane_feed(s, li, next == idx.size(), now_ns());
+            if (next == idx.size() && l.backlog.empty() &&
+                (l.forming < 0 || l.slots[l.forming].n_txns == 0))
+                break;                                   // everything launched
         }
-        status[li] = st;
-        if (st) message[li] = gcc_last_error();
+        if (st) halt(li, 2 * li, st);
     };
-    if (nl == 1) {
-        run_lane(0);
-    } else {
+    auto completer = [&](uint32_t li) {
+        if (cudaSetDevice(s->device) != cudaSuccess) {
+            halt(li, 2 * li + 1, fail(GCC_ERR_CUDA, "cannot select device"));
+            return;
+        }
+        const Lane& l = s->lanes[li];
+        const uint64_t want = mine[li].size();
+        while (!stopped(li) && __atomic_load_n(&l.trace_done, __ATOMIC_ACQUIRE) < want) {
+            const gcc_status st = lane_collect(s, li);
+            if (st) { halt(li, 2 * li + 1, st); return; }
+        }
+    };
+    {
         std::vector<std::thread> workers;
-        workers.reserve(nl);
-        for (uint32_t li = 0; li < nl; ++li) workers.emplace_back(run_lane, li);
+        workers.reserve(2 * nl);
+        for (uint32_t li = 0; li < nl; ++li) {
+            workers.emplace_back(feeder, li);
+            workers.emplace_back(completer, li);
+        }
         for (std::thread& w : workers) w.join();
     }
     gcc_status st = GCC_OK;
-    for (uint32_t li = 0; li < nl && !st; ++li)
-        if (status[li]) st = fail(status[li], "lane %u: %s", li, message[li].c_str());
+    for (uint32_t w = 0; w < 2 * nl && !st; ++w)
+        if (status[w]) st = fail(status[w], "lane %u: %s", w / 2, message[w].c_str());
     s->trace_out = nullptr;
     s->trace_reads = nullptr;
     s->trace_txns = nullptr;
