@@ -13,7 +13,12 @@ negative controls, and the check must find a counterexample for each: OCC
 with the commit timestamp taken together with (not after) the write locks,
 2PL with the ticket taken before the lock point, basic TO reading without
 checking wts again after the value, and TicToc reading (wts, value, rts)
-without re-checking wts.
+without re-checking wts.  The same check covers the orders in which writers
+read a record's value (TO: between the word and the dirty mark; multi-version
+TO: the slot's newest version between the head and the pending mark) with
+the read placed before the word or head as the negative control, and OCC's
+group commit (a unit of members committed in one tenure of their shared
+record) with the in-unit composition dropped as the negative control.
 """
 import random
 import sys
@@ -228,7 +233,11 @@ def tpl_txn(m, ops, out, tid, wait_die=False, ticket_first=False):
 DIRTY = 1 << 61
 
 
-def to_txn(m, ops, out, recheck=True):
+def to_txn(m, ops, out, recheck=True, write_value="before_mark"):
+    """write_value: where a writer reads the record's value -- "before_mark"
+    (the design: after the word, before the CAS that marks it dirty; kept if
+    that CAS succeeds), "after_mark" (under the mark) or "before_word" (a
+    rejected order: the value before the word it is paired with)."""
     ts = m.clock + 1
     m.clock += 1
     yield
@@ -253,20 +262,28 @@ def to_txn(m, ops, out, recheck=True):
             else:
                 fail = True
         else:
-            w_r, w_w = m.rts[r], m.word[r]              # one 128-bit load
+            if write_value == "before_word":
+                x = m.val[r]
+                yield
+            w_r, w_w = m.rts[r], m.word[r]              # one 128-bit load (acquire)
             yield
             if (w_w & DIRTY) or ts < w_r or ts < w_w:
                 fail = True
-            elif m.rts[r] == w_r and m.word[r] == w_w:  # the CAS
-                m.word[r] = DIRTY | ts
-                saved[r] = w_w
-                yield
-                x = m.val[r]
-                yield
-                reads[r] = x
-                newv[r] = x + d
             else:
-                fail = True
+                if write_value == "before_mark":
+                    x = m.val[r]
+                    yield
+                if m.rts[r] == w_r and m.word[r] == w_w:    # the CAS
+                    m.word[r] = DIRTY | ts
+                    saved[r] = w_w
+                    yield
+                    if write_value == "after_mark":
+                        x = m.val[r]
+                        yield
+                    reads[r] = x
+                    newv[r] = x + d
+                else:
+                    fail = True
         if fail:
             break
     if fail:
@@ -387,6 +404,17 @@ def test_to_read_without_the_wts_recheck_is_not_serializable():
     make = lambda m, ops, out, i: to_txn(m, ops, out, recheck=False)
     bad = sum(_count_violations(make, SCENARIOS[n], 4000)[0] for n in SCENARIOS)
     assert bad > 0
+
+
+def test_to_writer_value_orders():
+    """The writer's value read under the mark and read before it (between
+    the word and the CAS) are both serializable; read before the word, a
+    writer that commits in between pairs an old value with a new word."""
+    for order in ("after_mark", "before_mark"):
+        make = lambda m, ops, out, i: to_txn(m, ops, out, write_value=order)
+        assert sum(_count_violations(make, SCENARIOS[n], 4000)[0] for n in SCENARIOS) == 0
+    make = lambda m, ops, out, i: to_txn(m, ops, out, write_value="before_word")
+    assert sum(_count_violations(make, SCENARIOS[n], 4000)[0] for n in SCENARIOS) > 0
 
 
 def test_wait_die_lets_the_older_transaction_wait():
@@ -946,8 +974,11 @@ class SlotMV:
         self.clock = 0
 
 
-def _slot_value(m, r, f, ts):
-    e = m.slot.get((r, f), 0)
+def _slot_value(m, r, f, ts, e=None):
+    """The newest version of slot (r, f) older than ts, walking from pointer e
+    (read now when not given)."""
+    if e is None:
+        e = m.slot.get((r, f), 0)
     while e:
         wts, nxt, _, _, value = m.store[e - 1]
         if wts < ts:
@@ -956,14 +987,28 @@ def _slot_value(m, r, f, ts):
     return m.table[r][f]
 
 
-def slot_mvto_txn(m, ops, out, pointers_before_heads=True, writer_reads_table=False):
+def slot_mvto_txn(m, ops, out, pointers_before_heads=True, writer_reads_table=False,
+                  reads_before_mark=True, versions_before_head=False):
+    """reads_before_mark (the design): a writer reads its slot's newest version
+    after the head and before the CAS that installs it as pending (kept if
+    that CAS succeeds), and a reader takes its slot's pointer before the CAS
+    that raises rts.  versions_before_head: the rejected order, the version
+    read before the head it is checked against."""
     m.clock += 1
     ts = m.clock
     yield
     reads, pending = {}, {}
     fail = False
+    def newest(r, f):                                   # pointer, then its entry or the table
+        e = m.slot.get((r, f), 0)
+        return e, (m.table[r][f] if (writer_reads_table or not e) else m.store[e - 1][4])
+
     for (r, f, d) in ops:
         for _ in range(3):
+            if versions_before_head:
+                pe = m.slot.get((r, f), 0)
+                e, old = newest(r, f)
+                yield
             h = m.head[r]                               # one 16-byte load
             w, rt, pend = h
             yield
@@ -971,26 +1016,35 @@ def slot_mvto_txn(m, ops, out, pointers_before_heads=True, writer_reads_table=Fa
                 if pend and pend < ts:
                     fail = True
                     break
+                if reads_before_mark and not versions_before_head:
+                    pe = m.slot.get((r, f), 0)          # the pointer beside the rts CAS
+                    yield
                 if w < ts and rt < ts:
                     if m.head[r] != h:                  # CAS raising rts
                         yield
                         continue
                     m.head[r] = (w, ts, pend)
                     yield
-                reads[(r, f)] = _slot_value(m, r, f, ts)
+                if reads_before_mark or versions_before_head:
+                    reads[(r, f)] = _slot_value(m, r, f, ts, pe)
+                else:
+                    reads[(r, f)] = _slot_value(m, r, f, ts)
                 yield
                 break
             if pend or w >= ts or rt > ts:
                 fail = True
                 break
+            if reads_before_mark and not versions_before_head:
+                e, old = newest(r, f)
+                yield
             if m.head[r] != h:                          # CAS installing the pending writer
                 yield
                 continue
             m.head[r] = (w, rt, ts)
             yield
-            e = m.slot.get((r, f), 0)
-            old = m.table[r][f] if (writer_reads_table or not e) else m.store[e - 1][4]
-            yield
+            if not reads_before_mark and not versions_before_head:
+                e, old = newest(r, f)
+                yield
             reads[(r, f)] = old
             pending[r] = (f, old + d, e)
             break
@@ -1066,13 +1120,25 @@ def test_slot_mvcc_layout_is_serializable(name):
     assert commits > 0
 
 
+def test_slot_mvcc_reads_under_the_mark_are_serializable_too():
+    """The earlier order (a writer reads its slot's newest version after the
+    pending mark, a reader its pointer after the rts raise) replays as well."""
+    for n in DEV_SCENARIOS:
+        bad, commits = _slot_runs(DEV_SCENARIOS[n], 2000, reads_before_mark=False)
+        assert bad == 0 and commits > 0
+
+
 @pytest.mark.parametrize("variant", [dict(pointers_before_heads=False),
-                                     dict(writer_reads_table=True)],
-                         ids=["heads before pointers", "writer reads the table slot"])
+                                     dict(writer_reads_table=True),
+                                     dict(versions_before_head=True)],
+                         ids=["heads before pointers", "writer reads the table slot",
+                              "versions read before the head"])
 def test_slot_mvcc_negative_controls(variant):
     """A head published before its slots' pointers lets a newer reader take a
     superseded version; a writer that reads the table slot instead of the
-    slot's newest version loses updates.  Each must produce violations."""
+    slot's newest version loses updates; a version read before the head it is
+    checked against can be superseded by a commit in between.  Each must
+    produce violations."""
     bad = sum(_slot_runs(DEV_SCENARIOS[n], 3000, **variant)[0] for n in DEV_SCENARIOS)
     assert bad > 0
 
@@ -1227,3 +1293,158 @@ def test_early_locks_take_fewer_rounds_on_a_hot_batch():
         plain = sum(run_batch_rounds(hot_batch(s, read_ratio=rr), 64, s, 0)[0] for s in range(6))
         early = sum(run_batch_rounds(hot_batch(s, read_ratio=rr), 64, s, 1)[0] for s in range(6))
         assert early < plain, (rr, early, plain)
+
+
+# ---------------------------------------------------------------------------
+# OCC group commit (key-value batches): a unit of member transactions runs as
+# one attempt -- every member's reads (version, then value), one lock CAS per
+# distinct written record from the version its lowest op saw, consecutive
+# timestamps for the members still in, per-member validation of the reads of
+# records the unit does not hold, then each held record evaluated in member
+# order over the committing members (a member's read returns the value after
+# the earlier members' writes), written once and published once with the
+# last writer's timestamp + 1.  Units and single OCC transactions interleave
+# on the same records; every committed member, replayed in timestamp order,
+# must read what it read.  The negative control drops the composition: each
+# member reads and adds to the value its own read saw.
+# ---------------------------------------------------------------------------
+def occ_unit_txn(m, members, outs, compose=True):
+    ops_all = [(mi, r, d) for mi, ops in enumerate(members) for (r, d) in ops]
+    obs, val = {}, {}
+    dead = set()
+    for k, (mi, r, d) in enumerate(ops_all):            # read phase
+        v1 = m.word[r]
+        yield
+        if v1 & LOCK:
+            dead.add(mi)
+            continue
+        val[k] = m.val[r]
+        obs[k] = v1
+        yield
+    rep = {}
+    for k, (mi, r, d) in enumerate(ops_all):            # lowest op per record
+        rep.setdefault(r, k)
+    written = sorted({r for (_, r, d) in ops_all if d is not None})
+    held = {}
+    for r in written:                                    # one lock CAS per record
+        k = rep[r]
+        if k in obs and m.word[r] == obs[k]:
+            m.word[r] = obs[k] | LOCK
+            held[r] = obs[k]
+        yield
+    for (mi, r, d) in ops_all:
+        if d is not None and r not in held:
+            dead.add(mi)
+    alive = [mi for mi in range(len(members)) if mi not in dead]
+    ts_of = {}
+    if alive:
+        base = m.clock                                   # one atomic for all of them
+        m.clock += len(alive)
+        ts_of = {mi: base + i for i, mi in enumerate(alive)}
+        yield
+        for k, (mi, r, d) in enumerate(ops_all):         # validate reads not held
+            if mi in ts_of and r not in held:
+                ok = m.word[r] == obs[k]
+                yield
+                if not ok:
+                    dead.add(mi)
+    won = [mi for mi in alive if mi not in dead]
+    reads = {mi: {} for mi in won}
+    for k, (mi, r, d) in enumerate(ops_all):
+        if mi in reads and r not in held:
+            reads[mi][r] = val[k]
+    for r, v0 in held.items():                           # each held record, member order
+        cur, last = val[rep[r]], None
+        for mi in won:
+            for k, (mj, rr, d) in enumerate(ops_all):
+                if mj != mi or rr != r:
+                    continue
+                seen = cur if compose else val[k]
+                reads[mi][r] = seen
+                if d is not None:
+                    cur = seen + d
+                    last = ts_of[mi]
+        if last is not None:
+            m.val[r] = cur
+            yield
+            m.word[r] = last + 1
+        else:
+            m.word[r] = v0
+        yield
+    for mi in won:
+        outs[mi].append(((ts_of[mi],), reads[mi]))
+
+
+def run_actors(actors, initial, seed, compose=True):
+    """Interleave units and single OCC transactions; returns (committed
+    [(order key, reads, ops)], final values)."""
+    m = Mem(initial)
+    gens, members = [], []
+    for kind, body in actors:
+        if kind == "unit":
+            outs = [[] for _ in body]
+            gens.append(occ_unit_txn(m, body, outs, compose))
+            members += list(zip(body, outs))
+        else:
+            out = []
+            gens.append(occ_txn(m, body, out))
+            members.append((body, out))
+    live = list(range(len(gens)))
+    rng = random.Random(seed)
+    while live:
+        i = rng.choice(live)
+        try:
+            next(gens[i])
+        except StopIteration:
+            live.remove(i)
+    committed = [(o[0][0], o[0][1], ops) for ops, o in members if o]
+    return committed, m.val
+
+
+UNIT_SCENARIOS = {
+    "unit-vs-singles": [("unit", [[(0, 1), (1, None)], [(0, 2)]]),
+                        ("txn", [(0, 4), (1, 3)]), ("txn", [(1, None), (0, None)])],
+    "two-units": [("unit", [[(0, 1)], [(0, 2), (2, None)]]),
+                  ("unit", [[(0, 3), (1, None)], [(0, 4)]]), ("txn", [(2, 5)])],
+    "readers-inside": [("unit", [[(0, None), (1, 1)], [(0, 2)], [(1, None)]]),
+                       ("txn", [(0, 7)]), ("txn", [(1, None), (0, None)])],
+    "shared-others": [("unit", [[(0, 1), (2, 1)], [(0, 2), (2, None)], [(0, 3), (1, 5)]]),
+                      ("txn", [(2, 4), (1, None)])],
+}
+
+
+def _unit_violations(scenario, n, compose=True):
+    initial = [100, 200, 300]
+    bad = commits = 0
+    for seed in range(n):
+        committed, final = run_actors(scenario, initial, seed, compose)
+        commits += len(committed)
+        bad += not serial_replay_ok(committed, initial, final)
+    return bad, commits
+
+
+@pytest.mark.parametrize("name", sorted(UNIT_SCENARIOS))
+def test_occ_group_commit_unit_is_serializable(name):
+    bad, commits = _unit_violations(UNIT_SCENARIOS[name], 3000)
+    assert bad == 0
+    assert commits > 0
+
+
+def test_occ_group_commit_commits_several_members_per_tenure():
+    """Run alone, a unit commits every member in one tenure of the shared
+    record: the record's version moves once, by the last member's timestamp."""
+    m = Mem([100, 200, 300])
+    members = [[(0, 1)], [(0, 2), (1, None)], [(0, 4)]]
+    outs = [[] for _ in members]
+    for _ in occ_unit_txn(m, members, outs):
+        pass
+    assert all(outs)
+    assert m.val[0] == 107 and m.word[0] == 3            # timestamps 0, 1, 2
+    assert [o[0][1][0] for o in outs] == [100, 101, 103]
+
+
+def test_occ_group_commit_without_composition_is_not_serializable():
+    """Negative control: members that each read and add to their own read of
+    the shared record lose one another's writes."""
+    bad = sum(_unit_violations(UNIT_SCENARIOS[n], 3000, compose=False)[0] for n in UNIT_SCENARIOS)
+    assert bad > 0
