@@ -73,6 +73,12 @@ def parse_args(argv=None):
                    help="served form: most requests per rate (each rate runs at most 10 s "
                         "of arrivals)")
     p.add_argument("--kv-scheme", default="det", choices=SCHEMES, help="served form: key-value lane")
+    p.add_argument("--served-depth", type=int, default=4,
+                   help="served form: batches in flight per lane (1..8)")
+    p.add_argument("--served-delay-us", type=int, default=400,
+                   help="served form: longest wait of a batch's oldest request before launch")
+    p.add_argument("--served-max-batch", type=int, default=1 << 14,
+                   help="served form: transactions per batch at most")
     p.add_argument("--oe-scheme", default="det", choices=SCHEMES, help="served form: order-entry lane")
     return p.parse_args(argv)
 
@@ -231,7 +237,7 @@ CAPTURED_TRAFFIC = {
     # dram__bytes_write.sum,gpu__time_duration.sum (one pass), second
     # execute-kernel launch of `bench.py --steps 1 --warmup 1 --no-schemes
     # --no-e2e --no-cpu`: 3.51 GB read + 0.721 GB written
-    ("occ", 1 << 24, 1 << 20, 0.8, 0.5, 0, 0): (4_231_060_000, "b2c5644359ac0188"),
+    ("occ", 1 << 24, 1 << 20, 0.8, 0.5, 0, 0): (4_231_160_000, "c9ea0db5a26b39db"),
 }
 
 
@@ -716,7 +722,8 @@ def run_served(args, rank, world):
     oe0, oe, cap = wl.order_entry(seed=wl.SEEDS[4], W=8, n_txns=max(1, n_oe))  # every rate reloads it
     trace = wl.interleave([kv, oe], lane_of)
     gen_s = time.time() - t_gen
-    max_batch = 1 << 14
+    max_batch = args.served_max_batch
+    delay_ns = args.served_delay_us * 1000
     oe_scheme = args.oe_scheme
     results = []
 
@@ -735,8 +742,8 @@ def run_served(args, rank, world):
             sub = trace if m == n else wl.select(trace, np.arange(m))
             arrivals = wl.poisson_arrivals(wl.SEEDS[4] + int(rate), m, rate)
             dkv, doe = fresh()
-            srv = eng.Server([(dkv, args.kv_scheme, max_batch, 0, 100_000, 4),
-                              (doe, oe_scheme, max_batch, 0, 100_000, 4)])
+            srv = eng.Server([(dkv, args.kv_scheme, max_batch, 0, delay_ns, args.served_depth),
+                              (doe, oe_scheme, max_batch, 0, delay_ns, args.served_depth)])
             comp, _ = srv.run_trace(lane_of[:m], sub, arrivals)
             tots = [srv.lane_totals(0), srv.lane_totals(1)]
             srv.close()
@@ -783,7 +790,8 @@ def run_served(args, rank, world):
                                    f"{args.kv_scheme}) and order-entry (W=8, {oe_scheme}), "
                                    f"poisson arrivals, min({args.requests}, 10 s of arrivals) "
                                    f"requests per rate",
-                       "max_batch_txns": max_batch, "max_delay_us": 100, "depth": 4,
+                       "max_batch_txns": max_batch, "max_delay_us": args.served_delay_us,
+                       "depth": args.served_depth,
                        "trace_generation_s": round(gen_s, 1)},
             "p99_latency_us": sustained["p99_latency_us"],
             "p99_at_offered_txn_per_s": sustained["offered_txn_per_s"], "rates": results,

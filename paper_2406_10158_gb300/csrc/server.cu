@@ -322,10 +322,12 @@ gcc_status lane_feed(gcc_server* s, uint32_t li, bool flush_all, uint64_t t) {
         append(l.slots[l.forming], p.txn, pops, opd_of(p), wbytes, p.arrival, p.id);
         l.backlog.pop_front();
     }
-    // a forming batch past its delay (or everything, when draining) launches
+    // a forming batch launches past its delay, at once when none of the
+    // lane's batches is in flight (waiting gains nothing while the lane's GPU
+    // work is idle), and always when draining
     if (l.forming >= 0) {
         Slot& sl = l.slots[l.forming];
-        if (sl.n_txns && (flush_all || t - sl.oldest >= l.cfg.max_delay_ns)) {
+        if (sl.n_txns && (flush_all || t - sl.oldest >= l.cfg.max_delay_ns || ring_empty(l))) {
             gcc_status st = launch(s, l);
             if (st) return st;
         }
