@@ -456,8 +456,11 @@ gcc_status gcc_multi_plan_destroy(gcc_multi_plan *plan);
 /* Served form: a request loop that forms batches continuously.  Each lane
  * serves one database: arriving transactions join the lane's forming batch
  * until its transaction cap or its write-set budget (16 bytes per writing op)
- * is reached, or until its oldest request has waited max_delay_ns; the batch
- * is then copied to the device, executed and copied back on the lane's own
+ * is reached, until its oldest request has waited max_delay_ns, or, sooner,
+ * as soon as none of the lane's batches is in flight (waiting gains nothing
+ * while the lane's device work is idle; under load batches grow up to the
+ * delay or the caps); the batch is then copied to the device, executed and
+ * copied back on the lane's own
  * streams while the next batch forms.  Up to `depth` batches per lane are in
  * flight; lanes run concurrently.  Batches of one lane execute in formation
  * order (batch_seq), so a lane's committed requests, in (batch_seq,
