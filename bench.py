@@ -690,6 +690,16 @@ def run_batched(args, rank, world, dist=None):
 # ---------------------------------------------------------------------------
 # served form: continuous batching of a Poisson trace
 # ---------------------------------------------------------------------------
+def sustained_rate(results):
+    """The row whose latency a serving system reports: the highest offered
+    rate it sustains (commits at least 98% of it), not saturation; the
+    highest committed rate when none is sustained."""
+    held = [r for r in results if r["committed_txn_per_s"] >= 0.98 * r["offered_txn_per_s"]]
+    if held:
+        return max(held, key=lambda r: r["offered_txn_per_s"])
+    return max(results, key=lambda r: r["committed_txn_per_s"])
+
+
 def run_served(args, rank, world):
     """Open-loop Poisson arrivals, 50/50 by count of key-value txns (2^24 x 8
     u64, 16 ops, Zipf 0.8, 80% reads) and order-entry txns (W = 8), each lane
@@ -778,10 +788,7 @@ def run_served(args, rank, world):
         dkv.close()
         doe.close()
     best = max(results, key=lambda r: r["committed_txn_per_s"])
-    # the latency figure of a serving system: at the highest offered rate it
-    # sustains (commits at least 98% of the offered rate), not at saturation
-    held = [r for r in results if r["committed_txn_per_s"] >= 0.98 * r["offered_txn_per_s"]]
-    sustained = max(held, key=lambda r: r["offered_txn_per_s"]) if held else best
+    sustained = sustained_rate(results)
     return {"metric": METRIC, "form": "served", "value": best["committed_txn_per_s"],
             "unit": "txn/s", "n_gpus": 1, "steps": len(rates), "warmup": 0,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -88,3 +88,14 @@ def test_order_entry_bytes_by_procedure():
     assert got["bytes"] == want
     assert got["new_orders"] == int(is_no.sum()) and got["lines"] == int(lines.sum())
     assert 900 < got["per_txn"] < 1400            # about 1.2 KB at 50/50 and 10 lines
+
+
+def test_served_latency_is_reported_at_the_highest_sustained_rate():
+    rows = [{"offered_txn_per_s": 1e5, "committed_txn_per_s": 1.0e5, "p99_latency_us": 300},
+            {"offered_txn_per_s": 1e7, "committed_txn_per_s": 0.99e7, "p99_latency_us": 4000},
+            {"offered_txn_per_s": 1e8, "committed_txn_per_s": 2.4e7, "p99_latency_us": 3e5}]
+    assert bench.sustained_rate(rows)["offered_txn_per_s"] == 1e7
+    rows[1]["committed_txn_per_s"] = 0.9e7            # 10^7 no longer sustained
+    assert bench.sustained_rate(rows)["offered_txn_per_s"] == 1e5
+    # nothing sustained: the highest committed rate
+    assert bench.sustained_rate(rows[2:])["offered_txn_per_s"] == 1e8
