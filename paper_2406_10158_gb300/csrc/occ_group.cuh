@@ -24,13 +24,15 @@
 // timestamps while holding them, so it is serializable as one transaction
 // whose members follow each other in timestamp order: each member's result is
 // the serial execution in commit order.  Members that dropped out retry in
-// the unit's next attempt; a member is never waited for.
+// the unit's next attempt, after the randomized backoff of the plain kernel
+// (and, once the unit has failed queue_after times, a turn in the retry
+// queue of the record it failed on); a member is never waited for.
 //
 // Units are formed before the launch (occ_group.cu): each transaction is
-// keyed by its written record with the most writes in the batch; the
-// transactions of one key, in id order, are cut into units of up to U.  A
-// unit is run by whichever group fetches its lowest id; its other members'
-// ids are skipped when fetched.
+// keyed by its written record with the most writes in the batch, if no other
+// record it touches is contended too; the transactions of one key, in id
+// order, are cut into units of up to U.  A unit is run by whichever group
+// fetches its lowest id; its other members' ids are skipped when fetched.
 #pragma once
 
 #include "exec_common.cuh"

@@ -3,7 +3,8 @@
 // Every lane owns a ring of `depth` batch slots, each with pinned host and
 // device buffers sized for a full batch.  Arriving transactions are copied
 // into the lane's forming slot; a slot launches when it is full (transaction
-// cap or write-set budget) or when its oldest request has waited max_delay.
+// cap or write-set budget), when its oldest request has waited max_delay, or
+// as soon as none of the lane's batches is in flight.
 // A launch is three stream-ordered steps on three streams per lane:
 //   h2d stream   : inputs host -> device, event `in`
 //   exec stream  : waits `in`, gcc_execute on the lane's database, event `exec`
